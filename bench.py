@@ -1,0 +1,427 @@
+"""Benchmark: Tucker-compressed FMM aggregation + disaggregation on one GB300.
+
+One step = one aggregation (Fig. 2b) + one disaggregation (Fig. 3b) of every
+group of the workload, i.e. one far-field matvec without the translation
+stage.  Default workload: PEC sphere of diameter 30 lambda (icosphere nu = 180:
+648,000 triangles, 972,000 RWGs), 2-lambda boxes, 6-digit FMM (L = 39, 40 x 80
+directions), Tucker tolerance 1e-6, one CN(0, 1) right-hand side.
+
+Printed (rank 0, one JSON line): ms per matvec of the Tucker path with inputs
+resident in HBM (`value`), the same through the host-buffer C-ABI call (`e2e`),
+the dense-far-field comparator on the same GPU, the roofline of the dominant
+kernel, the FP64 oracle timed on the host cores (`cpu_baseline`) and the SM
+clocks seen during the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload sphere30] [--no-dense] [--no-cpu-baseline]
+Under torchrun every rank runs an independent replica on its own GPU (the
+aggregation / disaggregation of one problem needs no exchange between GPUs).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "agg+disagg ms/matvec & HBM GB/s: Tucker vs dense far-fields, 1 GB300, rel err≤1e-6"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sphere30")
+    ap.add_argument("--no-dense", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-groups", type=int, default=3)
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload_desc(w, L=None, n_theta=None, n_phi=None, G=None):
+    d = (f"PEC sphere D={w.diameter:g} lambda, icosphere nu={w.nu} ({w.n_tri} triangles, {w.n_rwg} RWGs), "
+         f"{w.box:g}-lambda boxes, d0={w.digits} digits")
+    if L is not None:
+        d += f" (L={L}, {n_theta}x{n_phi} directions, {G} groups)"
+    d += f", Tucker tol {w.tol:g}, {w.nrhs if w.rhs != 'planewave_sweep' else 1} RHS CN(0,1) seed {w.seed}"
+    return d
+
+
+# ------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+        self.marks = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.dev)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append((time.time(), ln.strip()))
+
+    def mark(self, on):
+        self.marks.append((time.time(), on))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        windows = []
+        for i in range(0, len(self.marks) - 1, 2):
+            windows.append((self.marks[i][0], self.marks[i + 1][0]))
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for t, ln in self.lines:
+            if not any(a <= t <= b for a, b in windows):
+                continue
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ------------------------------------------------------------- cpu baseline
+def oracle_sample(w, verts, tris, n_groups_sample, seed):
+    """Oracle far-fields + T-HOSVD for a few groups of the workload (setup, untimed)."""
+    import oracle
+    P = oracle.problem.build(verts, tris, k=2 * math.pi, box=w.box, digits=w.digits, tol=w.tol,
+                             compress=False, keep_tensors=False)
+    G = P.groups.n_groups
+    pick = sorted(set(int(round(i * (G - 1) / max(n_groups_sample - 1, 1))) for i in range(n_groups_sample)))
+    tuck, dense = {}, {}
+    for g in pick:
+        At, Ap = P.group_tensors(g)
+        dense[g] = (At, Ap)
+        tuck[g] = (oracle.hosvd.thosvd(At, w.tol), oracle.hosvd.thosvd(Ap, w.tol))
+    x = None
+    return P, pick, tuck, dense
+
+
+def oracle_step(P, pick, tuck, x):
+    """Oracle Tucker aggregation + disaggregation of the sampled groups (complex128)."""
+    from oracle import apply
+    for g in pick:
+        ids = P.groups.members[g]
+        xg = x[ids]
+        F = [apply.tucker_aggregate(tuck[g][a], xg) for a in range(2)]
+        y = sum(apply.tucker_disaggregate(tuck[g][a], F[a], P.grid.weights) for a in range(2))
+    return y
+
+
+def time_oracle(P, pick, tuck, x, steps, warmup, budget_s=None):
+    for _ in range(warmup):
+        oracle_step(P, pick, tuck, x)
+    t = []
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        s = time.perf_counter()
+        oracle_step(P, pick, tuck, x)
+        t.append(time.perf_counter() - s)
+        n += 1
+        if budget_s is None and n >= steps:
+            break
+        if budget_s is not None and (time.perf_counter() - t0 >= budget_s and n >= 3):
+            break
+    G = P.groups.n_groups
+    # scale the sampled groups to the whole problem by their share of Tucker work
+    return 1e3 * statistics.median(t) * G / len(pick), n
+
+
+def cpu_threads():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        if info:
+            return max(i.get("num_threads", 1) for i in info)
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+# ---------------------------------------------------------------- reference
+def run_reference(args, w, world, rank):
+    if rank != 0:
+        return
+    from paper_2103_05822_gb300.inputs import complex_gaussian, icosphere
+    verts, tris = icosphere(w.diameter, w.nu)
+    P, pick, tuck, _ = oracle_sample(w, verts, tris, args.oracle_groups, w.seed)
+    x = complex_gaussian(P.n_rwg, w.seed)
+    ms, n = time_oracle(P, pick, tuck, x, args.steps, args.warmup)
+    cores = cpu_threads()
+    sample = (f"{len(pick)} of {P.groups.n_groups} groups (oracle far-field + T-HOSVD untimed); "
+              f"median of {n} steps of Tucker agg+disagg on them, scaled by groups to the whole sphere")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "complex128", "data": "synthetic",
+        "config": {"workload": workload_desc(w, P.grid.L, P.grid.n_theta, P.grid.n_phi, P.groups.n_groups)},
+        "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------- ours
+def traffic_record(kernel):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel source is unchanged since."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    src = os.path.join(ROOT, "paper_2103_05822_gb300", "csrc", "apply.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    ent = rec.get(kernel)
+    if not ent or ent.get("apply_cu_sha256") != sha:
+        return None
+    return ent.get("dram_bytes_per_launch_full")
+
+
+def run_ours(args, w, world, rank, local):
+    import torch
+    from paper_2103_05822_gb300 import tfmm
+    from paper_2103_05822_gb300.inputs import complex_gaussian, icosphere
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    verts, tris = icosphere(w.diameter, w.nu)
+    t0 = time.perf_counter()
+    mesh = tfmm.tfmm_mesh_create(verts, tris)
+    prm = tfmm.tfmm_params_default(k=2 * math.pi, box=w.box, digits=float(w.digits), tol=w.tol,
+                                   keep_dense=0 if args.no_dense else 1, max_rhs=1)
+    stream = torch.cuda.current_stream()
+    plan = tfmm.tfmm_plan_create(mesh, prm, stream=stream)
+    setup_s = time.perf_counter() - t0
+    info = plan.info
+    N, G, nd = info["n_rwg"], info["n_groups"], info["n_dir"]
+
+    x_host = complex_gaussian(N, w.seed).astype(np.complex64)
+    x = torch.from_numpy(x_host).to(dev)
+    spec = torch.empty((1, G, 2, nd), dtype=torch.complex64, device=dev)
+    y = torch.empty(N, dtype=torch.complex64, device=dev)
+
+    def step_tucker(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        tfmm.tfmm_aggregate(plan, x, spec, stream=stream)
+        if ev is not None:
+            ev[1].record(stream)
+        tfmm.tfmm_disaggregate(plan, spec, y, stream=stream)
+        if ev is not None:
+            ev[2].record(stream)
+
+    def step_dense(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        tfmm.tfmm_aggregate_dense(plan, x, spec, stream=stream)
+        if ev is not None:
+            ev[1].record(stream)
+        tfmm.tfmm_disaggregate_dense(plan, spec, y, stream=stream)
+        if ev is not None:
+            ev[2].record(stream)
+
+    def timed(step, K, W):
+        for _ in range(W):
+            step()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        clocks.mark(True)
+        start.record(stream)
+        for k in range(K):
+            step(evs[k])
+        end.record(stream)
+        torch.cuda.synchronize()
+        clocks.mark(False)
+        barrier()
+        total = start.elapsed_time(end)
+        agg = [e[0].elapsed_time(e[1]) for e in evs]
+        dis = [e[1].elapsed_time(e[2]) for e in evs]
+        return total, agg, dis
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    # untimed soak so that clocks settle under load
+    for _ in range(max(args.warmup, 3)):
+        step_tucker()
+    torch.cuda.synchronize()
+
+    total, agg, dis = timed(step_tucker, args.steps, args.warmup)
+    ms_step = total / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    value = total / (args.steps * world)  # whole-job ms per matvec (replicas run side by side)
+
+    dense = None
+    if not args.no_dense:
+        dtot, dagg, ddis = timed(step_dense, args.steps, args.warmup)
+        dense = {"ms_per_matvec": dtot / args.steps, "aggregate_ms": statistics.mean(dagg),
+                 "disaggregate_ms": statistics.mean(ddis)}
+
+    # end to end through the host-buffer C-ABI call: H2D x, agg, disagg, D2H y, sync
+    xh = torch.from_numpy(x_host).pin_memory()
+    yh = torch.empty(N, dtype=torch.complex64).pin_memory()
+    for _ in range(args.warmup):
+        tfmm.tfmm_matvec_host(plan, xh, yh, stream=stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks.mark(True)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        tfmm.tfmm_matvec_host(plan, xh, yh, stream=stream)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    clocks.mark(False)
+    barrier()
+    clocks.stop()
+
+    # accuracy of this run against the dense-far-field GPU path (same x)
+    rel = None
+    if dense is not None:
+        ref = torch.empty_like(spec)
+        tfmm.tfmm_aggregate(plan, x, spec, stream=stream)
+        tfmm.tfmm_aggregate_dense(plan, x, ref, stream=stream)
+        torch.cuda.synchronize()
+        rel = float(torch.linalg.vector_norm(spec - ref) / torch.linalg.vector_norm(ref))
+
+    # roofline of the dominant kernel (algorithmic bytes per launch / mean launch time)
+    fac = info["tucker_bytes_alg"]
+    bytes_agg = fac + 8 * N + 16 * G * nd
+    bytes_dis = fac + 16 * G * nd + 8 * N
+    agg_ms, dis_ms = statistics.mean(agg), statistics.mean(dis)
+    if agg_ms >= dis_ms:
+        kern, ms_k, bytes_k = "tucker_aggregate_kernel", agg_ms, bytes_agg
+    else:
+        kern, ms_k, bytes_k = "tucker_disaggregate_kernel", dis_ms, bytes_dis
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = bytes_k / (ms_k * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+            "traffic": traffic_record(kern), "algorithmic_bytes": bytes_k}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        P, pick, tuck, _ = oracle_sample(w, verts, tris, args.oracle_groups, w.seed)
+        ms_cpu, n = time_oracle(P, pick, tuck, x_host.astype(np.complex128), 0, 1, budget_s=10.0)
+        cpu = {"value": ms_cpu, "unit": "ms", "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"{len(pick)} of {G} groups, oracle Tucker agg+disagg (complex128) timed {n} times "
+                         f"(~10 s), median scaled by groups to the whole sphere; oracle setup untimed"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "complex64", "data": "synthetic",
+            "config": {"workload": workload_desc(w, info["L"], info["n_theta"], info["n_phi"], G),
+                       "l2": "no flush: Tucker factors ({:.2f} GB) exceed the 129 MB L2".format(fac / 1e9),
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+            "stages": {"aggregate_ms": agg_ms, "disaggregate_ms": dis_ms,
+                       "aggregate_gbs": bytes_agg / agg_ms / 1e6, "disaggregate_gbs": bytes_dis / dis_ms / 1e6},
+            "dense": dense,
+            "speedup_vs_dense": (dense["ms_per_matvec"] / ms_step) if dense else None,
+            "rel_err_vs_dense_gpu": rel,
+            "memory": {"tucker_bytes": info["tucker_bytes"], "tucker_bytes_alg": fac,
+                       "dense_bytes": 8 * 2 * N * nd, "compression": 8 * 2 * N * nd / fac,
+                       "max_rank": info["max_rank"], "max_n_beta": info["max_n_beta"]},
+            "setup_s": setup_s, "setup_ms": info["setup_ms"],
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clocks.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    from paper_2103_05822_gb300.inputs import WORKLOADS
+    w = WORKLOADS[args.workload]
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, w, world, rank)
+    else:
+        run_ours(args, w, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

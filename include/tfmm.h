@@ -1,0 +1,226 @@
+/*
+ * tfmm - Tucker-compressed FMM far-fields on one GPU (C ABI).
+ *
+ * The library implements the setup and the two per-iteration stages of
+ * "Compression of Far-Fields in the Fast Multipole Method via Tucker
+ * Decomposition" (Qian, Wang, Yucel, arXiv 2103.05822):
+ *
+ *   setup    RWG functions on a triangle mesh (Sec. II.A, ref. [20]); the
+ *            FMM-FFT box grid (Sec. II.A); the (L+1) x N_phi spherical grid
+ *            (Sec. II.A after Eq. 4); far-field tensors of every group (Eq. 4,
+ *            Fig. 1a); truncated HOSVD (Eq. 6, Sec. II.B).
+ *   hot path aggregation from the Tucker factors (Fig. 2b, replacing Eq. 3)
+ *            and disaggregation (Fig. 3b, replacing Eq. 5), plus the same two
+ *            stages from the uncompressed tensors (Eqs. 3 and 5) for comparison.
+ *
+ * Conventions used by every entry point:
+ *   - Complex numbers are interleaved pairs (re, im): tfmm_cfloat (8 bytes) on
+ *     the hot path, tfmm_cdouble (16 bytes) for setup inputs and exports.
+ *   - A "direction" index is i = i_theta + n_theta * i_phi (theta fastest).
+ *   - Right-hand-side blocks are column-major: x[n + ldx * r] is RWG n of RHS r.
+ *   - Spectra are laid out [R][G][2][n_phi][n_theta]: RHS r, group g, component
+ *     alpha (0 = theta, 1 = phi), direction i at
+ *     ((r * G + g) * 2 + alpha) * N_dir + i.  Groups are the non-empty boxes in
+ *     ascending linear box index ix + Kx (iy + Ky iz).
+ *   - Pointers documented "device" must be CUDA device (or managed) memory on
+ *     the current device; "host" pointers are ordinary CPU memory.  The caller
+ *     owns every buffer it passes; the library copies what it keeps.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Hot-path calls are asynchronous on that stream; calls on one
+ *     plan must be ordered on one stream (a plan's work queue is shared).
+ *   - Every function returns a tfmm_status and never aborts the process.
+ *     tfmm_last_error() returns a message for the last failure of the calling
+ *     thread.  Asynchronous kernel faults surface at the next call that
+ *     synchronises.
+ */
+#ifndef TFMM_H
+#define TFMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TFMM_OK = 0,
+    TFMM_INVALID_ARG = 1, /* bad pointer, size, layout or parameter */
+    TFMM_OOM = 2,         /* device or host allocation failed */
+    TFMM_CUDA = 3,        /* CUDA runtime / cuBLAS / cuSOLVER error */
+    TFMM_NUMERIC = 4,     /* eigen-solver failure or non-finite data */
+    TFMM_NOT_BUILT = 5,   /* the requested data was not built (e.g. dense tensors) */
+    TFMM_IO = 6           /* checkpoint file could not be read or written */
+} tfmm_status;
+
+typedef struct { float re, im; } tfmm_cfloat;
+typedef struct { double re, im; } tfmm_cdouble;
+
+typedef struct tfmm_mesh tfmm_mesh;
+typedef struct tfmm_plan tfmm_plan;
+
+/* Setup parameters (Sec. II.A and III).  Fill with tfmm_params_default(). */
+typedef struct {
+    double k;          /* wavenumber 2 pi / lambda (> 0) */
+    double box;        /* FMM box edge a (> 0), same length unit as the mesh */
+    double digits;     /* FMM accuracy d0 in digits (> 0), sets L (Sec. II.A) */
+    int32_t nphi_rule; /* 0: N_phi = 2L+1 (the paper), 1: N_phi = 2(L+1) */
+    int32_t L_override;/* > 0: use this L instead of the bandwidth formula */
+    double tol;        /* Tucker tolerance gamma (>= 0), truncation gamma/sqrt(3) per mode */
+    int32_t quad_order;/* collapsed Gauss-Legendre order per triangle, 1..10 (default 5) */
+    int32_t keep_dense;/* nonzero: also keep FP32 uncompressed tensors (Eqs. 3, 5) */
+    int32_t max_rhs;   /* largest R later passed to the hot path (>= 1) */
+    int32_t batch_groups; /* groups per setup batch (0 = automatic) */
+    int32_t reserved[6];
+} tfmm_params;
+
+typedef struct {
+    int32_t L, n_theta, n_phi, n_dir;
+    int32_t n_groups;
+    int32_t K[3];             /* box grid K_x, K_y, K_z */
+    int64_t n_rwg;
+    int32_t max_n_beta;
+    int32_t max_rank[3];      /* largest r_theta, r_phi, r_beta over groups and alpha */
+    int64_t tucker_bytes;     /* FP32 factors + cores as stored (with padding) */
+    int64_t tucker_bytes_alg; /* FP32 factors + cores without padding */
+    int64_t dense_bytes;      /* FP32 uncompressed tensors (0 if not kept) */
+    double setup_ms[4];       /* far-field, HOSVD, packing, total */
+} tfmm_plan_info;
+
+/* Default parameters: k = 2 pi, box 0.5, 3 digits, N_phi = 2(L+1), gamma 1e-4,
+ * quadrature order 5, no dense copy, max_rhs 1. */
+tfmm_status tfmm_params_default(tfmm_params* p);
+
+/* Message of the last failure on this thread ("" if none).  Valid until the
+ * thread's next tfmm call. */
+const char* tfmm_last_error(void);
+
+/* ------------------------------------------------------------------ mesh -- */
+/* Builds the RWG functions of a triangle mesh (Sec. II.A, ref. [20]).
+ * verts: host, nv x 3 doubles (row-major).  tris: host, nt x 3 vertex ids.
+ * Every edge shared by exactly two triangles carries one RWG; RWGs are
+ * numbered by (min vertex id, max vertex id) of their edge, ascending; T+ is
+ * the adjacent triangle with the lower index.  The arrays are copied.
+ * Errors: INVALID_ARG for null pointers, nv < 3, nt < 1, out-of-range or
+ * repeated vertex ids in a triangle, degenerate (zero-area) triangles. */
+tfmm_status tfmm_mesh_create(const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                             tfmm_mesh** out);
+tfmm_status tfmm_mesh_num_rwg(const tfmm_mesh* mesh, int64_t* n_rwg);
+/* Host outputs, each n_rwg x 2 (row-major): edge vertex ids, (T+, T-) triangle
+ * ids, free vertex ids (p+, p-).  Any output may be NULL. */
+tfmm_status tfmm_mesh_rwg(const tfmm_mesh* mesh, int64_t* edge, int64_t* tri, int64_t* free_vertex);
+tfmm_status tfmm_mesh_destroy(tfmm_mesh* mesh);
+
+/* ------------------------------------------------------------------ plan -- */
+/* Runs the whole setup on the current GPU: box grid and groups (Sec. II.A),
+ * bandwidth L and grid, far-field tensors by Eq. 4 in FP64, truncated
+ * sequential HOSVD (Eq. 6) in FP64, FP32 packing of factors and cores for the
+ * hot path, and (keep_dense) the FP32 uncompressed tensors.  `stream` orders
+ * the setup work; the call returns after the setup has finished.
+ * Errors: INVALID_ARG (parameters), OOM, CUDA, NUMERIC. */
+tfmm_status tfmm_plan_create(const tfmm_mesh* mesh, const tfmm_params* p, void* stream, tfmm_plan** out);
+
+/* Builds a plan from Tucker factors given by the caller instead of running the
+ * setup (Eq. 6 data, e.g. from another compressor or a checkpoint).
+ *   n_rwg         total RWG count (x / y length)
+ *   n_groups      G; n_theta, n_phi: grid sizes (N_dir = n_theta n_phi)
+ *   group_offsets host, G+1 ascending offsets into group_rwg
+ *   group_rwg     host, global RWG ids of each group; every id in 0..n_rwg-1
+ *                 appears exactly once over all groups
+ *   ranks         host, G x 2 x 3: (r_theta, r_phi, r_beta) per group and alpha
+ *   factors       host, FP64 complex, for g = 0..G-1, alpha = 0, 1 in turn:
+ *                 U_theta (n_theta x r_theta), U_phi (n_phi x r_phi),
+ *                 U_beta (n_beta x r_beta), core (r_theta x r_phi x r_beta),
+ *                 each column-major and packed back to back
+ *   weights       host, N_dir quadrature weights (NULL: all ones)
+ *   max_rhs       largest R the hot path will be called with
+ * Errors: INVALID_ARG for inconsistent sizes or ranks outside
+ * 1 <= r <= n, OOM, CUDA. */
+tfmm_status tfmm_plan_from_tucker(int64_t n_rwg, int32_t n_groups, int32_t n_theta, int32_t n_phi,
+                                  const int64_t* group_offsets, const int64_t* group_rwg,
+                                  const int32_t* ranks, const tfmm_cdouble* factors,
+                                  const double* weights, int32_t max_rhs, void* stream,
+                                  tfmm_plan** out);
+
+/* Adds uncompressed tensors to a plan (for the dense stages of Eqs. 3 and 5).
+ * tensors: host, FP64 complex, for g, alpha in turn an n_theta x n_phi x n_beta
+ * column-major tensor A[i_theta, i_phi, n] = P^{alpha,+}_{n,i} (Fig. 1a). */
+tfmm_status tfmm_plan_set_dense(tfmm_plan* plan, const tfmm_cdouble* tensors, void* stream);
+
+tfmm_status tfmm_plan_info_get(const tfmm_plan* plan, tfmm_plan_info* info);
+/* n_beta and ranks (r_theta, r_phi, r_beta) of group g, component alpha. */
+tfmm_status tfmm_plan_group(const tfmm_plan* plan, int32_t g, int32_t alpha, int64_t* n_beta,
+                            int32_t* ranks3);
+/* Host outputs: offsets (G+1) and global RWG ids (n_rwg) of the groups. */
+tfmm_status tfmm_plan_members(const tfmm_plan* plan, int64_t* offsets, int64_t* rwg_ids);
+/* Host output: box centres r_v, G x 3 (row-major); NULL-safe no-op for plans
+ * built from factors (INVALID_ARG). */
+tfmm_status tfmm_plan_centres(const tfmm_plan* plan, double* centres);
+/* Host outputs: theta (n_theta), w_theta (n_theta, Gauss-Legendre in cos
+ * theta), phi (n_phi); *w_phi = 2 pi / n_phi.  Any may be NULL. */
+tfmm_status tfmm_plan_quadrature(const tfmm_plan* plan, double* theta, double* w_theta, double* phi,
+                                 double* w_phi);
+/* Copies the FP64 factors of (g, alpha) to host buffers sized by
+ * tfmm_plan_group (column-major, as in tfmm_plan_from_tucker). */
+tfmm_status tfmm_plan_export_factors(const tfmm_plan* plan, int32_t g, int32_t alpha, tfmm_cdouble* U_theta,
+                                     tfmm_cdouble* U_phi, tfmm_cdouble* U_beta, tfmm_cdouble* core);
+/* Recomputes the FP64 far-field tensors of group g (Eq. 4) on the GPU and
+ * copies them to host: A_theta and A_phi, each n_theta x n_phi x n_beta
+ * column-major.  Needs a plan made by tfmm_plan_create. */
+tfmm_status tfmm_plan_farfield(const tfmm_plan* plan, int32_t g, tfmm_cdouble* A_theta, tfmm_cdouble* A_phi,
+                               void* stream);
+tfmm_status tfmm_plan_destroy(tfmm_plan* plan);
+
+/* -------------------------------------------------------------- hot path -- */
+/* Aggregation (Eq. 3 evaluated as in Fig. 2b): for every group g and alpha,
+ * spectra[r][g][alpha] = U_theta (U_phi (C x_3 (U_beta^T x_g))^T)^T, the
+ * N_dir far-field of the group's currents.
+ *   x       device, n_rwg x R column-major FP32 complex, leading dimension ldx >= n_rwg
+ *   R       1 <= R <= max_rhs
+ *   spectra device, R x G x 2 x N_dir FP32 complex, overwritten
+ * Errors: INVALID_ARG (null pointers, R out of range, ldx < n_rwg), CUDA. */
+tfmm_status tfmm_aggregate(tfmm_plan* plan, const tfmm_cfloat* x, int32_t R, int64_t ldx, tfmm_cfloat* spectra,
+                           void* stream);
+
+/* Disaggregation (Eq. 5 evaluated as in Fig. 3b), the weighted adjoint of
+ * tfmm_aggregate:  y = beta y + sum_alpha A_alpha^H (W .* g_alpha)  with W the
+ * quadrature weights (apply_weights != 0) or ones (apply_weights == 0, the
+ * plain conjugate transpose of Eq. 5).
+ *   spectra device, as produced by tfmm_aggregate
+ *   y       device, n_rwg x R column-major, leading dimension ldy >= n_rwg
+ *   beta    scale of the old y; beta = 0 overwrites y (old NaNs are dropped)
+ * Errors: INVALID_ARG, CUDA. */
+tfmm_status tfmm_disaggregate(tfmm_plan* plan, const tfmm_cfloat* spectra, int32_t R, int32_t apply_weights,
+                              tfmm_cfloat beta, tfmm_cfloat* y, int64_t ldy, void* stream);
+
+/* The same two stages from the uncompressed FP32 tensors (Eqs. 3 and 5).
+ * Errors as above, plus NOT_BUILT when the plan holds no dense tensors. */
+tfmm_status tfmm_aggregate_dense(tfmm_plan* plan, const tfmm_cfloat* x, int32_t R, int64_t ldx,
+                                 tfmm_cfloat* spectra, void* stream);
+tfmm_status tfmm_disaggregate_dense(tfmm_plan* plan, const tfmm_cfloat* spectra, int32_t R, int32_t apply_weights,
+                                    tfmm_cfloat beta, tfmm_cfloat* y, int64_t ldy, void* stream);
+
+/* Aggregation followed by disaggregation of the spectra it produced, from and
+ * to HOST buffers: copies x (host, n_rwg x R column-major, ld n_rwg) to the
+ * device, aggregates, disaggregates with weights and beta = 0, copies y back
+ * to host (n_rwg x R) and synchronises `stream`.  The translation stage
+ * between them is not part of this library: the outgoing spectra are used as
+ * incoming spectra.  dense != 0 uses the uncompressed tensors.  Device
+ * buffers are owned by the plan and allocated on the first call for a given R.
+ * Errors: INVALID_ARG, NOT_BUILT, OOM, CUDA. */
+tfmm_status tfmm_matvec_host(tfmm_plan* plan, const tfmm_cfloat* x_host, tfmm_cfloat* y_host, int32_t R,
+                             int32_t dense, void* stream);
+
+/* RWG-tested plane-wave excitations (Eq. 2): V[m + n_rwg r] =
+ * -int b_m(r') . pol_r exp(-j k khat_r . r') dr' for R incidences.
+ *   khat, pol  host, R x 3 (row-major) propagation directions and polarisations
+ *   V          device, n_rwg x R FP32 complex
+ * Errors: INVALID_ARG, CUDA.  Needs a plan made by tfmm_plan_create. */
+tfmm_status tfmm_planewave(const tfmm_plan* plan, const double* khat, const double* pol, int32_t R,
+                           tfmm_cfloat* V, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TFMM_H */

@@ -1,0 +1,158 @@
+// Internal declarations shared by the tfmm translation units (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/tfmm.h"
+
+namespace tfmm {
+
+struct Error : std::runtime_error {
+    tfmm_status code;
+    Error(tfmm_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+[[noreturn]] inline void fail(tfmm_status c, const std::string& m) { throw Error(c, m); }
+
+#define TFMM_CUDA_CHECK(call)                                                                       \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) {                                                                    \
+            if (e_ == cudaErrorMemoryAllocation)                                                    \
+                ::tfmm::fail(TFMM_OOM, std::string(#call) + ": " + cudaGetErrorString(e_));         \
+            ::tfmm::fail(TFMM_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));            \
+        }                                                                                           \
+    } while (0)
+
+#define TFMM_REQUIRE(cond, msg)                                                                     \
+    do {                                                                                            \
+        if (!(cond)) ::tfmm::fail(TFMM_INVALID_ARG, msg);                                           \
+    } while (0)
+
+// ----------------------------------------------------------------------- mesh
+struct Mesh {
+    int64_t nv = 0, nt = 0;
+    std::vector<double> verts;   // nv x 3
+    std::vector<int32_t> tris;   // nt x 3
+    int64_t n_rwg = 0;
+    std::vector<int64_t> edge;   // n_rwg x 2, ascending vertex ids
+    std::vector<int64_t> tri;    // n_rwg x 2, (T+, T-)
+    std::vector<int64_t> freev;  // n_rwg x 2, (p+, p-)
+    std::vector<double> length;  // n_rwg
+};
+
+// RWG geometry as the far-field kernels read it: p+, p-, q1, q2 (edge ends), l.
+struct RwgGeom {
+    double pp[3], pm[3], q1[3], q2[3];
+    double l, pad[3];
+};
+
+// ---------------------------------------------------------------- hot layout
+// One (group, alpha) work item of the Tucker kernels.  Offsets count complex
+// elements in the packed FP32 factor buffer; every array starts 16-byte aligned.
+struct TuckerItem {
+    int64_t ub;    // U_beta^T: r_b rows of ld_nb (row c = column c of U_beta)
+    int64_t core;  // C_(3): r_b rows of ld_ab, entry a + r_t b
+    int64_t uphi;  // U_phi, n_phi x r_p column-major
+    int64_t uth;   // U_theta, n_theta x r_t column-major
+    int64_t rwg;   // offset of the group's RWG ids
+    int32_t n_beta, ld_nb, rt, rp, rb, ld_ab, g, alpha;
+};
+
+// One (group, alpha) uncompressed tensor: n_beta rows of ld_dir (row n = P_n^{alpha,+}).
+struct DenseItem {
+    int64_t a;
+    int64_t rwg;
+    int32_t n_beta, g, alpha, pad;
+};
+
+struct Schedule {
+    int threads = 512;
+    int blocks = 0;       // persistent grid
+    size_t smem = 0;      // dynamic shared memory per CTA
+};
+
+// ----------------------------------------------------------------------- plan
+struct HostFactors64 {     // FP64 factors of one (g, alpha), device memory
+    double2* base = nullptr;  // U_theta | U_phi | U_beta | core (column-major, back to back)
+    int rt = 0, rp = 0, rb = 0;
+};
+
+struct Plan {
+    // grid
+    int L = 0, n_theta = 0, n_phi = 0, n_dir = 0, ld_dir = 0;
+    std::vector<double> theta, w_theta, phi;
+    double w_phi = 0.0;
+    std::vector<float> weights;         // n_dir
+    double k = 0.0;
+    // groups
+    int G = 0;
+    int64_t N = 0;
+    int K[3] = {1, 1, 1};
+    std::vector<int64_t> grp_off;      // G + 1
+    std::vector<int64_t> grp_rwg;      // N
+    std::vector<double> centres;       // G x 3
+    std::vector<int32_t> ranks;        // G x 2 x 3
+    bool has_geometry = false;
+    tfmm_params params{};
+    double setup_ms[4] = {0, 0, 0, 0};
+
+    // device: common
+    int* d_grp_rwg = nullptr;          // N (int32 global RWG ids, group order)
+    float* d_weights = nullptr;        // n_dir
+    unsigned int* d_counters = nullptr;// work-queue tickets (self-resetting)
+    int num_sms = 0;
+    // device: Tucker
+    float2* d_factors = nullptr;
+    int64_t factor_elems = 0, factor_elems_alg = 0;
+    TuckerItem* d_items = nullptr;     // G x 2, (g, alpha) order
+    int* d_agg_order = nullptr;        // item ids, longest first
+    int* d_dis_order = nullptr;        // group ids, longest first
+    std::vector<TuckerItem> items;
+    Schedule agg_sched, dis_sched;
+    int max_nb = 0, max_ldnb = 0, max_rank[3] = {0, 0, 0}, max_ldab = 0;
+    // device: dense
+    float2* d_dense = nullptr;
+    int64_t dense_elems = 0;
+    DenseItem* d_dense_items = nullptr;
+    int* d_dense_agg_order = nullptr;
+    int* d_dense_dis_order = nullptr;
+    Schedule dagg_sched, ddis_sched;
+    // device: geometry for recomputation / excitation
+    RwgGeom* d_geom = nullptr;         // N, global RWG order
+    std::vector<RwgGeom> geom;
+    // FP64 factors (exports)
+    std::vector<HostFactors64> f64;    // G x 2
+    // workspace of tfmm_matvec_host
+    int ws_R = 0;
+    float2 *d_ws_x = nullptr, *d_ws_spec = nullptr, *d_ws_y = nullptr;
+
+    ~Plan();
+};
+
+// setup.cu
+void build_tucker_setup(Plan& P, const Mesh& M, cudaStream_t s);
+void farfield_group_host(const Plan& P, int g, double2* At, double2* Ap, cudaStream_t s);
+void planewave_rhs(const Plan& P, const double* khat, const double* pol, int R, float2* V, cudaStream_t s);
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
+
+// apply.cu
+void finalize_hot_layout(Plan& P, cudaStream_t s);  // items, schedules, orders (factors already packed)
+void finalize_dense_layout(Plan& P);
+void launch_tucker_aggregate(const Plan& P, const float2* x, int R, int64_t ldx, float2* spec, cudaStream_t s);
+void launch_tucker_disaggregate(const Plan& P, const float2* spec, int R, int weights, float2 beta, float2* y,
+                                int64_t ldy, cudaStream_t s);
+void launch_dense_aggregate(const Plan& P, const float2* x, int R, int64_t ldx, float2* spec, cudaStream_t s);
+void launch_dense_disaggregate(const Plan& P, const float2* spec, int R, int weights, float2 beta, float2* y,
+                               int64_t ldy, cudaStream_t s);
+void pack_factors_fp32(Plan& P, cudaStream_t s);  // from P.f64 into P.d_factors
+void pack_dense_fp32_from_f64(Plan& P, const double2* src, int g, int alpha, cudaStream_t s);
+
+inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+}  // namespace tfmm

@@ -1,0 +1,784 @@
+// Setup stage on the GPU (Sec. II.A-B): far-field tensors of every group
+// (Eq. 4) in FP64, then a sequentially truncated HOSVD (Eq. 6) in FP64.
+//
+// Far-field: P^{alpha,+}_{n,i} = alpha_i . int b_n(r) exp(+j k k_i.(r - r_v)) dr,
+// by a collapsed (Duffy) Gauss-Legendre rule on each of the two triangles of
+// the RWG; alpha_i is orthogonal to k_i, so the (I - k k) projector drops out.
+//
+// HOSVD: the factor of each mode is the leading eigenvector block of the Gram
+// matrix of that mode's unfolding (left singular vectors of the unfolding),
+// truncated where the discarded eigenvalue sum drops to (gamma^2/3) ||A||_F^2,
+// which is the per-mode gamma/sqrt(3) rule of Sec. III.A and gives
+// ||A - A_hat||_F <= gamma ||A||_F.  The modes are processed in the order
+// theta, phi, beta and each later unfolding is that of the tensor already
+// projected on the earlier factors (sequential truncation; same bound as the
+// plain HOSVD of ref. [26]).  For the beta mode the smaller of the two Gram
+// matrices Z Z^H (n_beta) and Z^H Z (r_theta r_phi) is decomposed; in the
+// second case the factor is re-orthonormalised by a Householder QR.
+#include <cublas_v2.h>
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+
+#include "internal.h"
+
+namespace tfmm {
+
+namespace {
+
+#define CUBLAS_CHECK(call)                                                                          \
+    do {                                                                                            \
+        cublasStatus_t st_ = (call);                                                                \
+        if (st_ != CUBLAS_STATUS_SUCCESS)                                                           \
+            fail(st_ == CUBLAS_STATUS_ALLOC_FAILED ? TFMM_OOM : TFMM_CUDA,                          \
+                 std::string(#call) + " failed with cuBLAS status " + std::to_string((int)st_));   \
+    } while (0)
+
+#define CUSOLVER_CHECK(call)                                                                        \
+    do {                                                                                            \
+        cusolverStatus_t st_ = (call);                                                              \
+        if (st_ != CUSOLVER_STATUS_SUCCESS)                                                         \
+            fail(st_ == CUSOLVER_STATUS_ALLOC_FAILED ? TFMM_OOM : TFMM_CUDA,                        \
+                 std::string(#call) + " failed with cuSOLVER status " + std::to_string((int)st_)); \
+    } while (0)
+
+constexpr int kMaxQuad = 10;  // collapsed rule order cap: 100 points per triangle
+__constant__ double c_qu[kMaxQuad * kMaxQuad];
+__constant__ double c_qv[kMaxQuad * kMaxQuad];
+__constant__ double c_qw[kMaxQuad * kMaxQuad];
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    explicit DevBuf(size_t b) { alloc(b); }
+    void alloc(size_t b) {
+        release();
+        if (b == 0) return;
+        TFMM_CUDA_CHECK(cudaMalloc(&p, b));
+        bytes = b;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    ~DevBuf() { release(); }
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+// --------------------------------------------------------------- far-field
+constexpr int kFFThreads = 128;  // directions per block
+constexpr int kFFRwgs = 4;       // RWGs per block
+
+struct FFArgs {
+    const RwgGeom* geom;      // global RWG order
+    const int* grp_rwg;       // RWG ids, group order
+    const int64_t* rwg_off;   // per batch group: offset into grp_rwg
+    const int* nbeta;         // per batch group
+    const int64_t* out_off;   // per batch group: offset (double2) of its [alpha][n][i] block
+    const double* centre;     // per batch group, 3
+    const double* dirs;       // n_dir x 9: k_hat, theta_hat, phi_hat
+    double2* out;
+    double k;
+    int n_dir, nq;            // nq points per triangle
+};
+
+__global__ void __launch_bounds__(kFFThreads) farfield_kernel(const FFArgs a) {
+    __shared__ double s_pt[kFFRwgs][2 * kMaxQuad * kMaxQuad][3];
+    __shared__ double s_am[kFFRwgs][2 * kMaxQuad * kMaxQuad][3];
+    const int gb = blockIdx.z;
+    const int nb = a.nbeta[gb];
+    const int n0 = blockIdx.y * kFFRwgs;
+    if (n0 >= nb) return;
+    const int nr = min(kFFRwgs, nb - n0);
+    const double cx = a.centre[3 * gb], cy = a.centre[3 * gb + 1], cz = a.centre[3 * gb + 2];
+    const int npts = 2 * a.nq;
+    // quadrature points (relative to the box centre) and vector amplitudes
+    for (int e = threadIdx.x; e < nr * npts; e += blockDim.x) {
+        const int rr = e / npts, q = e % npts;
+        const RwgGeom g = a.geom[a.grp_rwg[a.rwg_off[gb] + n0 + rr]];
+        const int side = q >= a.nq;
+        const int qq = side ? q - a.nq : q;
+        const double* p = side ? g.pm : g.pp;
+        const double u = c_qu[qq], v = c_qv[qq], w = c_qw[qq];
+        const double sgn = side ? -1.0 : 1.0;
+        double r[3];
+        for (int c = 0; c < 3; ++c) {
+            r[c] = p[c] + u * (g.q1[c] - p[c]) + v * (1.0 - u) * (g.q2[c] - p[c]);
+            s_am[rr][q][c] = sgn * g.l * w * (r[c] - p[c]);
+        }
+        s_pt[rr][q][0] = r[0] - cx;
+        s_pt[rr][q][1] = r[1] - cy;
+        s_pt[rr][q][2] = r[2] - cz;
+    }
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n_dir) return;
+    const double* d = a.dirs + 9 * (int64_t)i;
+    const double kx = a.k * d[0], ky = a.k * d[1], kz = a.k * d[2];
+    for (int rr = 0; rr < nr; ++rr) {
+        double jr[3] = {0, 0, 0}, ji[3] = {0, 0, 0};
+        for (int q = 0; q < npts; ++q) {
+            const double psi = kx * s_pt[rr][q][0] + ky * s_pt[rr][q][1] + kz * s_pt[rr][q][2];
+            double sn, cs;
+            sincos(psi, &sn, &cs);
+            for (int c = 0; c < 3; ++c) {
+                jr[c] += s_am[rr][q][c] * cs;
+                ji[c] += s_am[rr][q][c] * sn;
+            }
+        }
+        const int n = n0 + rr;
+        double2* o = a.out + a.out_off[gb];
+        double2 pt, pp;
+        pt.x = d[3] * jr[0] + d[4] * jr[1] + d[5] * jr[2];
+        pt.y = d[3] * ji[0] + d[4] * ji[1] + d[5] * ji[2];
+        pp.x = d[6] * jr[0] + d[7] * jr[1] + d[8] * jr[2];
+        pp.y = d[6] * ji[0] + d[7] * ji[1] + d[8] * ji[2];
+        o[(int64_t)n * a.n_dir + i] = pt;
+        o[(int64_t)nb * a.n_dir + (int64_t)n * a.n_dir + i] = pp;
+    }
+}
+
+// ------------------------------------------------------------ small kernels
+// out[perm] of a 3-D column-major array in[i0 + d0 (i1 + d1 i2)].
+// mode 0: out[i0 + d0 (i2 + d2 i1)]  (swap the last two indices)
+// mode 1: out[i1 + d1 (i0 + d0 i2)]  (swap the first two indices)
+__global__ void permute3_kernel(const double2* __restrict__ in, double2* __restrict__ out, int d0, int d1,
+                                int d2, int mode) {
+    const int64_t total = (int64_t)d0 * d1 * d2;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i0 = (int)(e % d0);
+        const int64_t rest = e / d0;
+        const int i1 = (int)(rest % d1);
+        const int i2 = (int)(rest / d1);
+        int64_t o;
+        if (mode == 0)
+            o = i0 + (int64_t)d0 * (i2 + (int64_t)d2 * i1);
+        else
+            o = i1 + (int64_t)d1 * (i0 + (int64_t)d0 * i2);
+        out[o] = in[e];
+    }
+}
+
+// out (n x r, ld n) = rows 0..n-1 of columns lastcol, lastcol-1, ... of G (ld ldg),
+// i.e. the eigenvectors of the r largest eigenvalues, largest first; conj optional.
+__global__ void take_top_kernel(const double2* __restrict__ G, int ldg, int n, int lastcol, int r,
+                                double2* __restrict__ out, int conj_out) {
+    const int64_t total = (int64_t)n * r;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % n), j = (int)(e / n);
+        double2 v = G[i + (int64_t)ldg * (lastcol - j)];
+        if (conj_out) v.y = -v.y;
+        out[e] = v;
+    }
+}
+
+// Pads an n x n Gram matrix (lower part valid) into an nb x nb buffer: zeros off
+// the block, `diag` on the padded diagonal (below every true eigenvalue).
+__global__ void pad_gram_kernel(double2* __restrict__ G, int n, int nb, double diag) {
+    const int64_t total = (int64_t)nb * nb;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % nb), j = (int)(e / nb);
+        if (i < n && j < n) continue;
+        G[e] = make_double2(i == j ? diag : 0.0, 0.0);
+    }
+}
+
+// Copies an n x n lower triangle from src (ld n) into dst (ld nb).
+__global__ void copy_lower_kernel(const double2* __restrict__ src, int n, double2* __restrict__ dst, int nb) {
+    const int64_t total = (int64_t)n * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % n), j = (int)(e / n);
+        if (i >= j) dst[i + (int64_t)nb * j] = src[e];
+    }
+}
+
+// FP64 -> FP32 copy of an n x m column-major block into a buffer with leading dimension ldo.
+__global__ void to_f32_kernel(const double2* __restrict__ in, int64_t n, int64_t m, int64_t ldi,
+                              float2* __restrict__ out, int64_t ldo) {
+    const int64_t total = n * m;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e % n, j = e / n;
+        const double2 v = in[i + ldi * j];
+        out[i + ldo * j] = make_float2((float)v.x, (float)v.y);
+    }
+}
+
+// --------------------------------------------------------- plane-wave RHS
+struct PWArgs {
+    const RwgGeom* geom;
+    const double* khat;  // R x 3
+    const double* pol;   // R x 3
+    float2* V;
+    double k;
+    int64_t n;
+    int R, nq;
+};
+
+__global__ void planewave_kernel(const PWArgs a) {
+    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (m >= a.n) return;
+    const RwgGeom g = a.geom[m];
+    const double* kh = a.khat + 3 * r;
+    const double* p = a.pol + 3 * r;
+    double vr = 0.0, vi = 0.0;
+    for (int side = 0; side < 2; ++side) {
+        const double* pv = side ? g.pm : g.pp;
+        const double sgn = side ? -1.0 : 1.0;
+        for (int q = 0; q < a.nq; ++q) {
+            const double u = c_qu[q], v = c_qv[q], w = c_qw[q];
+            double r3[3], dot = 0.0, ph = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                r3[c] = pv[c] + u * (g.q1[c] - pv[c]) + v * (1.0 - u) * (g.q2[c] - pv[c]);
+                dot += sgn * g.l * w * (r3[c] - pv[c]) * p[c];
+                ph += kh[c] * r3[c];
+            }
+            double sn, cs;
+            sincos(-a.k * ph, &sn, &cs);
+            vr -= dot * cs;
+            vi -= dot * sn;
+        }
+    }
+    a.V[m + a.n * r] = make_float2((float)vr, (float)vi);
+}
+
+int grid1d(int64_t total, int threads = 256) {
+    int64_t b = (total + threads - 1) / threads;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, 65535 * 8));
+}
+
+void upload_quadrature(int order, cudaStream_t s) {
+    std::vector<double> x, w;
+    gauss_legendre(order, x, w);
+    std::vector<double> qu, qv, qw;
+    for (int a = 0; a < order; ++a)
+        for (int b = 0; b < order; ++b) {
+            const double u = 0.5 * (x[a] + 1.0), v = 0.5 * (x[b] + 1.0);
+            qu.push_back(u);
+            qv.push_back(v);
+            qw.push_back(0.25 * w[a] * w[b] * (1.0 - u));  // sum = 1/2: int_T f = 2A sum w f
+        }
+    TFMM_CUDA_CHECK(cudaMemcpyToSymbolAsync(c_qu, qu.data(), qu.size() * sizeof(double), 0,
+                                            cudaMemcpyHostToDevice, s));
+    TFMM_CUDA_CHECK(cudaMemcpyToSymbolAsync(c_qv, qv.data(), qv.size() * sizeof(double), 0,
+                                            cudaMemcpyHostToDevice, s));
+    TFMM_CUDA_CHECK(cudaMemcpyToSymbolAsync(c_qw, qw.data(), qw.size() * sizeof(double), 0,
+                                            cudaMemcpyHostToDevice, s));
+}
+
+std::vector<double> direction_table(const Plan& P) {
+    std::vector<double> dirs((size_t)P.n_dir * 9);
+    for (int ip = 0; ip < P.n_phi; ++ip)
+        for (int it = 0; it < P.n_theta; ++it) {
+            const double t = P.theta[it], ph = P.phi[ip];
+            const double st = std::sin(t), ct = std::cos(t), sp = std::sin(ph), cp = std::cos(ph);
+            double* d = &dirs[9 * ((size_t)it + (size_t)P.n_theta * ip)];
+            d[0] = st * cp; d[1] = st * sp; d[2] = ct;
+            d[3] = ct * cp; d[4] = ct * sp; d[5] = -st;
+            d[6] = -sp;     d[7] = cp;      d[8] = 0.0;
+        }
+    return dirs;
+}
+
+double ms_since(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// Smallest r >= 1 whose discarded eigenvalues (ascending list, clamped at 0) sum to <= thr2.
+int choose_rank(const double* ev, int n, double thr2) {
+    double tail = 0.0;
+    int r = n;
+    for (int i = 0; i < n; ++i) {  // discard i+1 smallest
+        tail += std::max(ev[i], 0.0);
+        if (tail <= thr2 && n - (i + 1) >= 1)
+            r = n - (i + 1);
+        else
+            break;
+    }
+    return std::max(r, 1);
+}
+
+// Batched Hermitian eigen-decomposition of `count` n x n matrices (lower part
+// valid, ld n, stride n*n) with eigenvalues ascending in W (count x n).
+// Uses the batched solver when the library accepts the size, else one Xsyevd per
+// matrix (TFMM_EIG=single forces the latter).
+void eig_batched(cusolverDnHandle_t sol, cusolverDnParams_t prm, double2* A, double* W, int n, int count,
+                 cudaStream_t s) {
+    if (count == 0) return;
+    size_t dbytes = 0, hbytes = 0;
+    DevBuf info(sizeof(int) * count);
+    const char* env = std::getenv("TFMM_EIG");
+    const bool force_single = env && std::strcmp(env, "single") == 0;
+    cusolverStatus_t st = CUSOLVER_STATUS_NOT_SUPPORTED;
+    if (!force_single)
+        st = cusolverDnXsyevBatched_bufferSize(sol, prm, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n,
+                                               CUDA_C_64F, A, n, CUDA_R_64F, W, CUDA_C_64F, &dbytes, &hbytes, count);
+    if (st == CUSOLVER_STATUS_SUCCESS) {
+        DevBuf work(std::max<size_t>(dbytes, 16));
+        std::vector<char> hwork(std::max<size_t>(hbytes, 16));
+        CUSOLVER_CHECK(cusolverDnXsyevBatched(sol, prm, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n,
+                                              CUDA_C_64F, A, n, CUDA_R_64F, W, CUDA_C_64F, work.p, dbytes,
+                                              hwork.data(), hbytes, info.as<int>(), count));
+    } else {
+        CUSOLVER_CHECK(cusolverDnXsyevd_bufferSize(sol, prm, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n,
+                                                   CUDA_C_64F, A, n, CUDA_R_64F, W, CUDA_C_64F, &dbytes, &hbytes));
+        DevBuf work(std::max<size_t>(dbytes, 16));
+        std::vector<char> hwork(std::max<size_t>(hbytes, 16));
+        for (int i = 0; i < count; ++i)
+            CUSOLVER_CHECK(cusolverDnXsyevd(sol, prm, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, CUDA_C_64F,
+                                            A + (int64_t)i * n * n, n, CUDA_R_64F, W + (int64_t)i * n, CUDA_C_64F,
+                                            work.p, dbytes, hwork.data(), hbytes, info.as<int>() + i));
+    }
+    std::vector<int> hinfo(count);
+    TFMM_CUDA_CHECK(cudaMemcpyAsync(hinfo.data(), info.p, sizeof(int) * count, cudaMemcpyDeviceToHost, s));
+    TFMM_CUDA_CHECK(cudaStreamSynchronize(s));
+    for (int i = 0; i < count; ++i)
+        if (hinfo[i] != 0) fail(TFMM_NUMERIC, "eigen-decomposition failed (info " + std::to_string(hinfo[i]) + ")");
+}
+
+struct Tensor {      // one (group, alpha) tensor of the current batch
+    int g, alpha, nb;
+    double2* A;      // n_theta x n_phi x nb
+    double norm2 = 0;
+    int rt = 0, rp = 0, rb = 0;
+};
+
+}  // namespace
+
+// Gauss-Legendre nodes and weights on [-1, 1], nodes ascending, by Newton's
+// iteration on the three-term recurrence of P_n (Golub & Welsch give the same
+// rule as eigenvalues of the Jacobi matrix).
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double z = std::cos(pi * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int l = 2; l <= n; ++l) {
+                const double p2 = ((2.0 * l - 1.0) * z * p1 - (l - 1.0) * p0) / l;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (n == 1) { p1 = z; p0 = 1.0; }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        // recompute the derivative at the converged node
+        double p0 = 1.0, p1 = z;
+        for (int l = 2; l <= n; ++l) {
+            const double p2 = ((2.0 * l - 1.0) * z * p1 - (l - 1.0) * p0) / l;
+            p0 = p1;
+            p1 = p2;
+        }
+        if (n == 1) { p1 = z; p0 = 1.0; }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        x[i] = -z;
+        x[n - 1 - i] = z;
+        w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+    if (n % 2 == 1) x[n / 2] = 0.0;
+}
+
+void build_tucker_setup(Plan& P, const Mesh& M, cudaStream_t s) {
+    (void)M;
+    const auto t_all = std::chrono::steady_clock::now();
+    const tfmm_params& prm = P.params;
+    const int nt = P.n_theta, np = P.n_phi, nd = P.n_dir;
+    const bool keep_dense = prm.keep_dense != 0;
+    TFMM_REQUIRE(prm.quad_order >= 1 && prm.quad_order <= kMaxQuad, "quad_order must be in 1..10");
+    upload_quadrature(prm.quad_order, s);
+    const int nq = prm.quad_order * prm.quad_order;
+
+    // geometry and directions
+    TFMM_CUDA_CHECK(cudaMalloc(&P.d_geom, sizeof(RwgGeom) * std::max<int64_t>(P.N, 1)));
+    TFMM_CUDA_CHECK(cudaMemcpyAsync(P.d_geom, P.geom.data(), sizeof(RwgGeom) * P.N, cudaMemcpyHostToDevice, s));
+    const std::vector<double> dirs = direction_table(P);
+    DevBuf d_dirs(sizeof(double) * dirs.size());
+    TFMM_CUDA_CHECK(cudaMemcpyAsync(d_dirs.p, dirs.data(), sizeof(double) * dirs.size(), cudaMemcpyHostToDevice, s));
+
+    // dense FP32 copy
+    if (keep_dense) {
+        P.dense_elems = (int64_t)P.ld_dir * P.N * 2;
+        TFMM_CUDA_CHECK(cudaMalloc(&P.d_dense, sizeof(float2) * std::max<int64_t>(P.dense_elems, 1)));
+    }
+
+    cublasHandle_t blas;
+    cusolverDnHandle_t sol;
+    cusolverDnParams_t sprm;
+    CUBLAS_CHECK(cublasCreate(&blas));
+    CUBLAS_CHECK(cublasSetStream(blas, s));
+    CUSOLVER_CHECK(cusolverDnCreate(&sol));
+    CUSOLVER_CHECK(cusolverDnSetStream(sol, s));
+    CUSOLVER_CHECK(cusolverDnCreateParams(&sprm));
+    struct Guard {
+        cublasHandle_t b; cusolverDnHandle_t s; cusolverDnParams_t p;
+        ~Guard() { cusolverDnDestroyParams(p); cusolverDnDestroy(s); cublasDestroy(b); }
+    } guard{blas, sol, sprm};
+
+    // batches of groups bounded by a device-memory budget
+    size_t free_b = 0, total_b = 0;
+    TFMM_CUDA_CHECK(cudaMemGetInfo(&free_b, &total_b));
+    const double per_rwg = 16.0 * nd * 2 * 3.2;  // tensors + projections + Grams, both alpha
+    const double budget = std::min<double>(0.35 * (double)free_b, 48e9);
+    int64_t rwg_budget = (int64_t)std::max(1.0, budget / per_rwg);
+    if (prm.batch_groups > 0) rwg_budget = INT64_MAX;
+
+    P.f64.assign((size_t)P.G * 2, HostFactors64{});
+    P.ranks.assign((size_t)P.G * 6, 0);
+    double ms_ff = 0, ms_svd = 0;
+
+    const double r_one = 1.0, r_zero = 0.0;  // herk scalars
+    const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0), zero = make_cuDoubleComplex(0.0, 0.0);
+    int g0 = 0;
+    while (g0 < P.G) {
+        int g1 = g0;
+        int64_t rw = 0;
+        while (g1 < P.G) {
+            const int64_t nb = P.grp_off[g1 + 1] - P.grp_off[g1];
+            if (g1 > g0 && (rw + nb > rwg_budget || (prm.batch_groups > 0 && g1 - g0 >= prm.batch_groups))) break;
+            rw += nb;
+            ++g1;
+        }
+        const int nbg = g1 - g0;
+        // ---- far-fields of the batch
+        auto t0 = std::chrono::steady_clock::now();
+        std::vector<int64_t> rwg_off(nbg), out_off(nbg);
+        std::vector<int> nbeta(nbg);
+        std::vector<double> cen(3 * nbg);
+        int64_t tot = 0;
+        int maxnb = 0;
+        for (int b = 0; b < nbg; ++b) {
+            const int g = g0 + b;
+            rwg_off[b] = P.grp_off[g];
+            nbeta[b] = (int)(P.grp_off[g + 1] - P.grp_off[g]);
+            maxnb = std::max(maxnb, nbeta[b]);
+            out_off[b] = tot;
+            tot += (int64_t)2 * nd * nbeta[b];
+            for (int c = 0; c < 3; ++c) cen[3 * b + c] = P.centres[3 * g + c];
+        }
+        DevBuf d_A(sizeof(double2) * tot);
+        DevBuf d_rwg_off(sizeof(int64_t) * nbg), d_out_off(sizeof(int64_t) * nbg), d_nb(sizeof(int) * nbg),
+            d_cen(sizeof(double) * 3 * nbg);
+        TFMM_CUDA_CHECK(cudaMemcpyAsync(d_rwg_off.p, rwg_off.data(), sizeof(int64_t) * nbg, cudaMemcpyHostToDevice, s));
+        TFMM_CUDA_CHECK(cudaMemcpyAsync(d_out_off.p, out_off.data(), sizeof(int64_t) * nbg, cudaMemcpyHostToDevice, s));
+        TFMM_CUDA_CHECK(cudaMemcpyAsync(d_nb.p, nbeta.data(), sizeof(int) * nbg, cudaMemcpyHostToDevice, s));
+        TFMM_CUDA_CHECK(cudaMemcpyAsync(d_cen.p, cen.data(), sizeof(double) * 3 * nbg, cudaMemcpyHostToDevice, s));
+        FFArgs fa;
+        fa.geom = P.d_geom;
+        fa.grp_rwg = P.d_grp_rwg;
+        fa.rwg_off = d_rwg_off.as<int64_t>();
+        fa.out_off = d_out_off.as<int64_t>();
+        fa.nbeta = d_nb.as<int>();
+        fa.centre = d_cen.as<double>();
+        fa.dirs = d_dirs.as<double>();
+        fa.out = d_A.as<double2>();
+        fa.k = P.k;
+        fa.n_dir = nd;
+        fa.nq = nq;
+        dim3 grid((nd + kFFThreads - 1) / kFFThreads, (maxnb + kFFRwgs - 1) / kFFRwgs, nbg);
+        farfield_kernel<<<grid, kFFThreads, 0, s>>>(fa);
+        TFMM_CUDA_CHECK(cudaGetLastError());
+        if (keep_dense) {
+            for (int b = 0; b < nbg; ++b)
+                for (int al = 0; al < 2; ++al) {
+                    const int64_t dst = ((int64_t)2 * P.grp_off[g0 + b] + (int64_t)al * nbeta[b]) * P.ld_dir;
+                    to_f32_kernel<<<grid1d((int64_t)nd * nbeta[b]), 256, 0, s>>>(
+                        d_A.as<double2>() + out_off[b] + (int64_t)al * nd * nbeta[b], nd, nbeta[b], nd,
+                        P.d_dense + dst, P.ld_dir);
+                }
+            TFMM_CUDA_CHECK(cudaGetLastError());
+        }
+        TFMM_CUDA_CHECK(cudaStreamSynchronize(s));
+        ms_ff += ms_since(t0);
+
+        // ---- HOSVD of the batch
+        t0 = std::chrono::steady_clock::now();
+        std::vector<Tensor> T;
+        for (int b = 0; b < nbg; ++b)
+            for (int al = 0; al < 2; ++al)
+                T.push_back(Tensor{g0 + b, al, nbeta[b], d_A.as<double2>() + out_off[b] + (int64_t)al * nd * nbeta[b]});
+        const int nT = (int)T.size();
+        const double tol2 = prm.tol * prm.tol / 3.0;
+
+        // mode theta: G1 = A_(1) A_(1)^H
+        DevBuf d_G1(sizeof(double2) * nT * nt * nt), d_W1(sizeof(double) * nT * nt);
+        for (int t = 0; t < nT; ++t)
+            CUBLAS_CHECK(cublasZherk(blas, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, nt, np * T[t].nb, &r_one,
+                                     (const cuDoubleComplex*)T[t].A, nt, &r_zero,
+                                     (cuDoubleComplex*)(d_G1.as<double2>() + (int64_t)t * nt * nt), nt));
+        eig_batched(sol, sprm, d_G1.as<double2>(), d_W1.as<double>(), nt, nT, s);
+        std::vector<double> W1((size_t)nT * nt);
+        TFMM_CUDA_CHECK(cudaMemcpyAsync(W1.data(), d_W1.p, sizeof(double) * W1.size(), cudaMemcpyDeviceToHost, s));
+        TFMM_CUDA_CHECK(cudaStreamSynchronize(s));
+        int64_t y1_tot = 0;
+        std::vector<int64_t> y1_off(nT);
+        for (int t = 0; t < nT; ++t) {
+            double n2 = 0;
+            for (int i = 0; i < nt; ++i) n2 += std::max(W1[(size_t)t * nt + i], 0.0);
+            T[t].norm2 = n2;
+            T[t].rt = choose_rank(&W1[(size_t)t * nt], nt, tol2 * n2);
+            y1_off[t] = y1_tot;
+            y1_tot += (int64_t)T[t].rt * np * T[t].nb;
+        }
+        // U_theta (n_theta x r_t), A1 = U_theta^H A_(1) -> [a, i_phi, n], Y1 = [a, n, i_phi]
+        DevBuf d_Ut(sizeof(double2) * nT * nt * nt);
+        DevBuf d_A1(sizeof(double2) * std::max<int64_t>(y1_tot, 1)), d_Y1(sizeof(double2) * std::max<int64_t>(y1_tot, 1));
+        for (int t = 0; t < nT; ++t) {
+            double2* Ut = d_Ut.as<double2>() + (int64_t)t * nt * nt;
+            take_top_kernel<<<grid1d((int64_t)nt * T[t].rt), 256, 0, s>>>(d_G1.as<double2>() + (int64_t)t * nt * nt, nt,
+                                                                           nt, nt - 1, T[t].rt, Ut, 0);
+            CUBLAS_CHECK(cublasZgemm(blas, CUBLAS_OP_C, CUBLAS_OP_N, T[t].rt, np * T[t].nb, nt, &one,
+                                     (const cuDoubleComplex*)Ut, nt, (const cuDoubleComplex*)T[t].A, nt, &zero,
+                                     (cuDoubleComplex*)(d_A1.as<double2>() + y1_off[t]), T[t].rt));
+            permute3_kernel<<<grid1d((int64_t)T[t].rt * np * T[t].nb), 256, 0, s>>>(d_A1.as<double2>() + y1_off[t],
+                                                          d_Y1.as<double2>() + y1_off[t], T[t].rt, np, T[t].nb, 0);
+        }
+        TFMM_CUDA_CHECK(cudaGetLastError());
+        d_A1.release();
+        // mode phi: G2' = Y1^H Y1 (= conj of the mode-2 Gram)
+        DevBuf d_G2(sizeof(double2) * nT * np * np), d_W2(sizeof(double) * nT * np);
+        for (int t = 0; t < nT; ++t)
+            CUBLAS_CHECK(cublasZherk(blas, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_C, np, T[t].rt * T[t].nb, &r_one,
+                                     (const cuDoubleComplex*)(d_Y1.as<double2>() + y1_off[t]), T[t].rt * T[t].nb,
+                                     &r_zero, (cuDoubleComplex*)(d_G2.as<double2>() + (int64_t)t * np * np), np));
+        eig_batched(sol, sprm, d_G2.as<double2>(), d_W2.as<double>(), np, nT, s);
+        std::vector<double> W2((size_t)nT * np);
+        TFMM_CUDA_CHECK(cudaMemcpyAsync(W2.data(), d_W2.p, sizeof(double) * W2.size(), cudaMemcpyDeviceToHost, s));
+        TFMM_CUDA_CHECK(cudaStreamSynchronize(s));
+        int64_t z_tot = 0;
+        std::vector<int64_t> z_off(nT);
+        for (int t = 0; t < nT; ++t) {
+            T[t].rp = choose_rank(&W2[(size_t)t * np], np, tol2 * T[t].norm2);
+            z_off[t] = z_tot;
+            z_tot += (int64_t)T[t].rt * T[t].rp * T[t].nb;
+        }
+        // V_r (n_phi x r_p); A2 = Y1 V_r -> [a, n, b]; Z = [n, a, b]; U_phi = conj(V_r)
+        DevBuf d_Vp(sizeof(double2) * nT * np * np), d_Up(sizeof(double2) * nT * np * np);
+        DevBuf d_A2(sizeof(double2) * std::max<int64_t>(z_tot, 1)), d_Z(sizeof(double2) * std::max<int64_t>(z_tot, 1));
+        for (int t = 0; t < nT; ++t) {
+            const int rt = T[t].rt, rp = T[t].rp, nb = T[t].nb;
+            double2* Vp = d_Vp.as<double2>() + (int64_t)t * np * np;
+            take_top_kernel<<<grid1d((int64_t)np * rp), 256, 0, s>>>(d_G2.as<double2>() + (int64_t)t * np * np, np, np,
+                                                                      np - 1, rp, Vp, 0);
+            take_top_kernel<<<grid1d((int64_t)np * rp), 256, 0, s>>>(d_G2.as<double2>() + (int64_t)t * np * np, np, np,
+                                                                      np - 1, rp, d_Up.as<double2>() + (int64_t)t * np * np, 1);
+            CUBLAS_CHECK(cublasZgemm(blas, CUBLAS_OP_N, CUBLAS_OP_N, rt * nb, rp, np, &one,
+                                     (const cuDoubleComplex*)(d_Y1.as<double2>() + y1_off[t]), rt * nb,
+                                     (const cuDoubleComplex*)Vp, np, &zero,
+                                     (cuDoubleComplex*)(d_A2.as<double2>() + z_off[t]), rt * nb));
+            permute3_kernel<<<grid1d((int64_t)rt * nb * rp), 256, 0, s>>>(d_A2.as<double2>() + z_off[t], d_Z.as<double2>() + z_off[t],
+                                                         rt, nb, rp, 1);
+        }
+        TFMM_CUDA_CHECK(cudaGetLastError());
+        d_Y1.release();
+        d_A2.release();
+        // mode beta: Gram of the smaller side of Z (n_beta x m, m = r_t r_p)
+        std::vector<int> n3(nT), bucket(nT);
+        for (int t = 0; t < nT; ++t) {
+            const int m = T[t].rt * T[t].rp;
+            n3[t] = std::min(T[t].nb, m);
+            bucket[t] = (int)round_up(n3[t], 32);
+        }
+        std::vector<int> bsizes(bucket);
+        std::sort(bsizes.begin(), bsizes.end());
+        bsizes.erase(std::unique(bsizes.begin(), bsizes.end()), bsizes.end());
+        std::vector<std::vector<double>> W3(nT);
+        std::vector<int64_t> gram_off(nT);
+        std::vector<int> gram_ld(nT);
+        DevBuf d_G3all;
+        {
+            int64_t g3_tot = 0;
+            for (int t = 0; t < nT; ++t) {
+                gram_off[t] = g3_tot;
+                gram_ld[t] = bucket[t];
+                g3_tot += (int64_t)bucket[t] * bucket[t];
+            }
+            d_G3all.alloc(sizeof(double2) * g3_tot);
+        }
+        DevBuf d_tmp;
+        for (int bs : bsizes) {
+            std::vector<int> members;
+            for (int t = 0; t < nT; ++t)
+                if (bucket[t] == bs) members.push_back(t);
+            // contiguous batch buffer for this bucket
+            DevBuf d_Gb(sizeof(double2) * (int64_t)members.size() * bs * bs), d_Wb(sizeof(double) * members.size() * bs);
+            for (size_t q = 0; q < members.size(); ++q) {
+                const int t = members[q];
+                const int rt = T[t].rt, rp = T[t].rp, nb = T[t].nb, m = rt * rp, n = n3[t];
+                double2* Gq = d_Gb.as<double2>() + (int64_t)q * bs * bs;
+                const double2* Z = d_Z.as<double2>() + z_off[t];
+                d_tmp.alloc(sizeof(double2) * (int64_t)n * n);
+                if (nb <= m)
+                    CUBLAS_CHECK(cublasZherk(blas, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, nb, m, &r_one,
+                                             (const cuDoubleComplex*)Z, nb, &r_zero, (cuDoubleComplex*)d_tmp.p, nb));
+                else
+                    CUBLAS_CHECK(cublasZherk(blas, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_C, m, nb, &r_one,
+                                             (const cuDoubleComplex*)Z, nb, &r_zero, (cuDoubleComplex*)d_tmp.p, m));
+                copy_lower_kernel<<<grid1d((int64_t)n * n), 256, 0, s>>>(d_tmp.as<double2>(), n, Gq, bs);
+                pad_gram_kernel<<<grid1d((int64_t)bs * bs), 256, 0, s>>>(Gq, n, bs, -(T[t].norm2 + 1.0));
+                TFMM_CUDA_CHECK(cudaStreamSynchronize(s));  // d_tmp is reused
+            }
+            TFMM_CUDA_CHECK(cudaGetLastError());
+            eig_batched(sol, sprm, d_Gb.as<double2>(), d_Wb.as<double>(), bs, (int)members.size(), s);
+            std::vector<double> Wb(members.size() * (size_t)bs);
+            TFMM_CUDA_CHECK(cudaMemcpyAsync(Wb.data(), d_Wb.p, sizeof(double) * Wb.size(), cudaMemcpyDeviceToHost, s));
+            for (size_t q = 0; q < members.size(); ++q)
+                TFMM_CUDA_CHECK(cudaMemcpyAsync(d_G3all.as<double2>() + gram_off[members[q]],
+                                                d_Gb.as<double2>() + (int64_t)q * bs * bs,
+                                                sizeof(double2) * (int64_t)bs * bs, cudaMemcpyDeviceToDevice, s));
+            TFMM_CUDA_CHECK(cudaStreamSynchronize(s));
+            for (size_t q = 0; q < members.size(); ++q) {
+                const int t = members[q];
+                // padded eigenvalues come first (they are negative); the true ones are the last n3
+                W3[t].assign(Wb.begin() + q * bs + (bs - n3[t]), Wb.begin() + (q + 1) * bs);
+            }
+        }
+        d_tmp.release();
+        // factors and cores
+        for (int t = 0; t < nT; ++t) {
+            const int rt = T[t].rt, rp = T[t].rp, nb = T[t].nb, m = rt * rp, n = n3[t], bs = gram_ld[t];
+            T[t].rb = choose_rank(W3[t].data(), n, tol2 * T[t].norm2);
+            const int rb = T[t].rb;
+            HostFactors64& F = P.f64[(size_t)T[t].g * 2 + T[t].alpha];
+            F.rt = rt; F.rp = rp; F.rb = rb;
+            const int64_t e_ut = (int64_t)nt * rt, e_up = (int64_t)np * rp, e_ub = (int64_t)nb * rb,
+                          e_c = (int64_t)m * rb;
+            TFMM_CUDA_CHECK(cudaMalloc(&F.base, sizeof(double2) * (e_ut + e_up + e_ub + e_c)));
+            double2* Ut = F.base;
+            double2* Up = Ut + e_ut;
+            double2* Ub = Up + e_up;
+            double2* Cc = Ub + e_ub;
+            TFMM_CUDA_CHECK(cudaMemcpyAsync(Ut, d_Ut.as<double2>() + (int64_t)t * nt * nt, sizeof(double2) * e_ut,
+                                            cudaMemcpyDeviceToDevice, s));
+            TFMM_CUDA_CHECK(cudaMemcpyAsync(Up, d_Up.as<double2>() + (int64_t)t * np * np, sizeof(double2) * e_up,
+                                            cudaMemcpyDeviceToDevice, s));
+            const double2* Z = d_Z.as<double2>() + z_off[t];
+            const double2* G3 = d_G3all.as<double2>() + gram_off[t];
+            if (nb <= m) {
+                // U_beta = leading eigenvectors of Z Z^H: rows 0..nb-1 of the last columns of the
+                // padded problem (its padding eigenvalues are negative and come first)
+                take_top_kernel<<<grid1d(e_ub), 256, 0, s>>>(G3, bs, nb, bs - 1, rb, Ub, 0);
+            } else {
+                // Q0 = Z V_r, then U_beta = orthonormal basis of Q0 (Householder QR)
+                DevBuf d_V(sizeof(double2) * (int64_t)m * rb), d_Q(sizeof(double2) * e_ub);
+                take_top_kernel<<<grid1d((int64_t)m * rb), 256, 0, s>>>(G3, bs, m, bs - 1, rb, d_V.as<double2>(), 0);
+                CUBLAS_CHECK(cublasZgemm(blas, CUBLAS_OP_N, CUBLAS_OP_N, nb, rb, m, &one,
+                                         (const cuDoubleComplex*)Z, nb, (const cuDoubleComplex*)d_V.p, m, &zero,
+                                         (cuDoubleComplex*)Ub, nb));
+                int lwork = 0, lwork2 = 0;
+                CUSOLVER_CHECK(cusolverDnZgeqrf_bufferSize(sol, nb, rb, (cuDoubleComplex*)Ub, nb, &lwork));
+                DevBuf d_tau(sizeof(double2) * rb), d_info(sizeof(int));
+                CUSOLVER_CHECK(cusolverDnZungqr_bufferSize(sol, nb, rb, rb, (cuDoubleComplex*)Ub, nb,
+                                                           (const cuDoubleComplex*)d_tau.p, &lwork2));
+                DevBuf d_work(sizeof(double2) * std::max(std::max(lwork, lwork2), 1));
+                CUSOLVER_CHECK(cusolverDnZgeqrf(sol, nb, rb, (cuDoubleComplex*)Ub, nb, (cuDoubleComplex*)d_tau.p,
+                                                (cuDoubleComplex*)d_work.p, std::max(lwork, lwork2), d_info.as<int>()));
+                CUSOLVER_CHECK(cusolverDnZungqr(sol, nb, rb, rb, (cuDoubleComplex*)Ub, nb,
+                                                (const cuDoubleComplex*)d_tau.p, (cuDoubleComplex*)d_work.p,
+                                                std::max(lwork, lwork2), d_info.as<int>()));
+                int hinfo = 0;
+                TFMM_CUDA_CHECK(cudaMemcpyAsync(&hinfo, d_info.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+                TFMM_CUDA_CHECK(cudaStreamSynchronize(s));
+                if (hinfo != 0) fail(TFMM_NUMERIC, "QR of the beta factor failed");
+            }
+            // core: C_(3) = U_beta^H Z (r_b x m), stored as the r_t x r_p x r_b tensor (m x r_b)
+            DevBuf d_C3(sizeof(double2) * e_c);
+            CUBLAS_CHECK(cublasZgemm(blas, CUBLAS_OP_C, CUBLAS_OP_N, rb, m, nb, &one, (const cuDoubleComplex*)Ub, nb,
+                                     (const cuDoubleComplex*)Z, nb, &zero, (cuDoubleComplex*)d_C3.p, rb));
+            CUBLAS_CHECK(cublasZgeam(blas, CUBLAS_OP_T, CUBLAS_OP_T, m, rb, &one, (const cuDoubleComplex*)d_C3.p, rb,
+                                     &zero, (const cuDoubleComplex*)d_C3.p, rb, (cuDoubleComplex*)Cc, m));
+            TFMM_CUDA_CHECK(cudaStreamSynchronize(s));  // temporaries of this tensor are released here
+            int* rk = &P.ranks[((size_t)T[t].g * 2 + T[t].alpha) * 3];
+            rk[0] = rt; rk[1] = rp; rk[2] = rb;
+        }
+        TFMM_CUDA_CHECK(cudaGetLastError());
+        TFMM_CUDA_CHECK(cudaStreamSynchronize(s));
+        ms_svd += ms_since(t0);
+        g0 = g1;
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    pack_factors_fp32(P, s);
+    TFMM_CUDA_CHECK(cudaStreamSynchronize(s));
+    P.setup_ms[0] = ms_ff;
+    P.setup_ms[1] = ms_svd;
+    P.setup_ms[2] = ms_since(t0);
+    P.setup_ms[3] = ms_since(t_all);
+}
+
+void farfield_group_host(const Plan& P, int g, double2* At, double2* Ap, cudaStream_t s) {
+    TFMM_REQUIRE(P.has_geometry && P.d_geom, "plan has no geometry (built from factors)");
+    TFMM_REQUIRE(g >= 0 && g < P.G, "group index out of range");
+    upload_quadrature(P.params.quad_order, s);
+    const int nb = (int)(P.grp_off[g + 1] - P.grp_off[g]);
+    const int nd = P.n_dir;
+    const std::vector<double> dirs = direction_table(P);
+    DevBuf d_dirs(sizeof(double) * dirs.size()), d_A(sizeof(double2) * 2 * (int64_t)nd * nb);
+    DevBuf d_rwg_off(sizeof(int64_t)), d_out_off(sizeof(int64_t)), d_nb(sizeof(int)), d_cen(sizeof(double) * 3);
+    const int64_t ro = P.grp_off[g], oo = 0;
+    TFMM_CUDA_CHECK(cudaMemcpyAsync(d_dirs.p, dirs.data(), sizeof(double) * dirs.size(), cudaMemcpyHostToDevice, s));
+    TFMM_CUDA_CHECK(cudaMemcpyAsync(d_rwg_off.p, &ro, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    TFMM_CUDA_CHECK(cudaMemcpyAsync(d_out_off.p, &oo, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    TFMM_CUDA_CHECK(cudaMemcpyAsync(d_nb.p, &nb, sizeof(int), cudaMemcpyHostToDevice, s));
+    TFMM_CUDA_CHECK(cudaMemcpyAsync(d_cen.p, &P.centres[3 * g], sizeof(double) * 3, cudaMemcpyHostToDevice, s));
+    FFArgs fa;
+    fa.geom = P.d_geom;
+    fa.grp_rwg = P.d_grp_rwg;
+    fa.rwg_off = d_rwg_off.as<int64_t>();
+    fa.out_off = d_out_off.as<int64_t>();
+    fa.nbeta = d_nb.as<int>();
+    fa.centre = d_cen.as<double>();
+    fa.dirs = d_dirs.as<double>();
+    fa.out = d_A.as<double2>();
+    fa.k = P.k;
+    fa.n_dir = nd;
+    fa.nq = P.params.quad_order * P.params.quad_order;
+    dim3 grid((nd + kFFThreads - 1) / kFFThreads, (nb + kFFRwgs - 1) / kFFRwgs, 1);
+    farfield_kernel<<<grid, kFFThreads, 0, s>>>(fa);
+    TFMM_CUDA_CHECK(cudaGetLastError());
+    TFMM_CUDA_CHECK(cudaMemcpyAsync(At, d_A.p, sizeof(double2) * (int64_t)nd * nb, cudaMemcpyDeviceToHost, s));
+    TFMM_CUDA_CHECK(cudaMemcpyAsync(Ap, d_A.as<double2>() + (int64_t)nd * nb, sizeof(double2) * (int64_t)nd * nb,
+                                    cudaMemcpyDeviceToHost, s));
+    TFMM_CUDA_CHECK(cudaStreamSynchronize(s));
+}
+
+void planewave_rhs(const Plan& P, const double* khat, const double* pol, int R, float2* V, cudaStream_t s) {
+    TFMM_REQUIRE(P.has_geometry && P.d_geom, "plan has no geometry (built from factors)");
+    upload_quadrature(P.params.quad_order, s);
+    DevBuf d_k(sizeof(double) * 3 * R), d_p(sizeof(double) * 3 * R);
+    TFMM_CUDA_CHECK(cudaMemcpyAsync(d_k.p, khat, sizeof(double) * 3 * R, cudaMemcpyHostToDevice, s));
+    TFMM_CUDA_CHECK(cudaMemcpyAsync(d_p.p, pol, sizeof(double) * 3 * R, cudaMemcpyHostToDevice, s));
+    PWArgs a;
+    a.geom = P.d_geom;
+    a.khat = d_k.as<double>();
+    a.pol = d_p.as<double>();
+    a.V = V;
+    a.k = P.k;
+    a.n = P.N;
+    a.R = R;
+    a.nq = P.params.quad_order * P.params.quad_order;
+    dim3 grid((unsigned)((P.N + 255) / 256), R);
+    planewave_kernel<<<grid, 256, 0, s>>>(a);
+    TFMM_CUDA_CHECK(cudaGetLastError());
+    TFMM_CUDA_CHECK(cudaStreamSynchronize(s));
+}
+
+}  // namespace tfmm

@@ -1,0 +1,105 @@
+"""C-ABI library: loads, exports what include/tfmm.h declares, host-side logic (no GPU)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_05822_gb300 import tfmm
+from paper_2103_05822_gb300.inputs import icosphere
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(tfmm.library_path()):
+        from paper_2103_05822_gb300 import build
+        build.build()
+    return tfmm.load()
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(tfmm_\w+)\s*\(", txt))
+    return names
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = _declared_functions()
+    assert len(declared) >= 20
+    missing = [n for n in declared if not hasattr(lib, n)]
+    assert not missing, missing
+    assert declared == set(tfmm.EXPORTED)
+
+
+def test_params_default(lib):
+    p = tfmm.tfmm_params_default()
+    assert abs(p.k - 2 * np.pi) < 1e-15 and p.quad_order == 5 and p.max_rhs == 1 and p.nphi_rule == 1
+
+
+@pytest.mark.parametrize("nu", [1, 4, 12])
+def test_rwg_table_matches_oracle_bit_exact(lib, nu):
+    v, f = icosphere(2.0, nu)
+    mesh = tfmm.tfmm_mesh_create(v, f)
+    edge, tri, free = tfmm.tfmm_mesh_rwg(mesh)
+    r = oracle.rwg.build_rwg(v, f)
+    assert np.array_equal(edge, r.edge)
+    assert np.array_equal(tri, r.tri)
+    assert np.array_equal(free, r.free)
+
+
+def test_open_and_nonmanifold_meshes(lib):
+    v = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 0], [0.5, 0.5, 1.0]], float)
+    # edge (1, 2) shared by three triangles: not an RWG; (0,1,2)-(1,3,2) pair would be
+    f = np.array([[0, 1, 2], [1, 3, 2], [1, 2, 4]])
+    mesh = tfmm.tfmm_mesh_create(v, f)
+    assert tfmm.tfmm_mesh_num_rwg(mesh) == len(oracle.rwg.build_rwg(v, f).length) == 0
+    mesh2 = tfmm.tfmm_mesh_create(v, f[:2])
+    assert tfmm.tfmm_mesh_num_rwg(mesh2) == 1
+
+
+@pytest.mark.parametrize("case", ["oob", "repeat", "degenerate", "nan"])
+def test_mesh_create_rejects_bad_input(lib, case):
+    v = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [2, 0, 0]], float)
+    f = np.array([[0, 1, 2]])
+    if case == "oob":
+        f = np.array([[0, 1, 7]])
+    elif case == "repeat":
+        f = np.array([[0, 1, 1]])
+    elif case == "degenerate":
+        f = np.array([[0, 1, 3]])  # collinear
+    elif case == "nan":
+        v[2, 1] = np.nan
+    with pytest.raises(tfmm.TfmmError) as e:
+        tfmm.tfmm_mesh_create(v, f)
+    assert e.value.status == tfmm.INVALID_ARG
+    assert len(lib.tfmm_last_error()) > 0
+
+
+def test_null_pointers_are_rejected(lib):
+    out = ctypes.c_void_p()
+    assert lib.tfmm_mesh_create(None, 3, None, 1, ctypes.byref(out)) == tfmm.INVALID_ARG
+    assert lib.tfmm_mesh_num_rwg(None, None) == tfmm.INVALID_ARG
+    assert lib.tfmm_plan_info_get(None, None) == tfmm.INVALID_ARG
+    assert lib.tfmm_aggregate(None, None, 1, 1, None, None) == tfmm.INVALID_ARG
+    assert lib.tfmm_params_default(None) == tfmm.INVALID_ARG
+    assert lib.tfmm_mesh_destroy(None) == tfmm.OK
+    assert lib.tfmm_plan_destroy(None) == tfmm.OK
+
+
+def test_plan_params_validated_before_any_gpu_work(lib):
+    v, f = icosphere(1.0, 2)
+    mesh = tfmm.tfmm_mesh_create(v, f)
+    for bad in ({"k": -1.0}, {"box": 0.0}, {"digits": 0.0}, {"tol": -1e-3}, {"quad_order": 11},
+                {"nphi_rule": 3}, {"max_rhs": 0}):
+        p = tfmm.tfmm_params_default(**bad)
+        with pytest.raises(tfmm.TfmmError) as e:
+            tfmm.tfmm_plan_create(mesh, p, stream=0)
+        assert e.value.status == tfmm.INVALID_ARG

@@ -1,0 +1,210 @@
+"""GPU parity of the hot-path kernels against the FP64 oracle (Figs. 2b, 3b; Eqs. 3, 5).
+
+The factors are seeded synthetic inputs with ragged shapes, given to both sides:
+the oracle applies the Tucker procedures in complex128, the library runs its
+FP32 kernels through the C ABI.  Tolerance: relative l2 error <= 1e-5 per
+output vector (FP32 storage of the factors, ~6e-8 each, and FP32
+accumulation over at most a few thousand terms).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import apply, hosvd
+from paper_2103_05822_gb300.inputs import complex_gaussian, synthetic_tucker
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def _tfmm():
+    from paper_2103_05822_gb300 import tfmm
+    return tfmm
+
+
+def _case(seed, n_theta, n_phi, nbetas, rank_fn):
+    rng = np.random.default_rng(seed)
+    ranks = [rank_fn(rng, nb) for nb in nbetas]
+    syn = synthetic_tucker(n_theta, n_phi, nbetas, ranks, seed)
+    n_rwg = sum(nbetas)
+    perm = rng.permutation(n_rwg)
+    members, pos = [], 0
+    for nb in nbetas:
+        members.append(np.sort(perm[pos:pos + nb]))
+        pos += nb
+    T = [[hosvd.Tucker(s.U_theta, s.U_phi, s.U_beta, s.core) for s in per] for per in syn]
+    factors = [[(t.U_theta, t.U_phi, t.U_beta, t.core) for t in per] for per in T]
+    return n_rwg, members, T, factors
+
+
+CASES = {
+    # name: (n_theta, n_phi, n_beta per group, rank function)
+    "tiny": (3, 6, [1, 2, 5], lambda rng, nb: [(1, 1, 1), (min(2, 3), 2, min(nb, 2))]),
+    "ragged": (14, 28, [77, 12, 98, 3, 64], lambda rng, nb: [
+        (int(rng.integers(1, 14)), int(rng.integers(1, 28)), int(rng.integers(1, nb + 1))) for _ in range(2)]),
+    "paper_like": (40, 80, [940, 1786, 411], lambda rng, nb: [
+        (int(rng.integers(24, 31)), int(rng.integers(28, 36)), int(rng.integers(170, 201))) for _ in range(2)]),
+    "odd_grid": (13, 25, [33, 50], lambda rng, nb: [(5, 7, 9), (13, 25, 33 if nb == 33 else 50)]),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def case(request):
+    tfmm = _tfmm()
+    nt, npf, nbetas, rank_fn = CASES[request.param]
+    n_rwg, members, T, factors = _case(100 + sorted(CASES).index(request.param), nt, npf, nbetas, rank_fn)
+    w = np.random.default_rng(5).uniform(0.05, 1.0, nt * npf)
+    plan = tfmm.tfmm_plan_from_tucker(n_rwg, nt, npf, members, factors, weights=w, max_rhs=4)
+    return dict(plan=plan, n_rwg=n_rwg, members=members, T=T, w=w, nt=nt, npf=npf, G=len(members))
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def test_aggregate_matches_oracle(case):
+    tfmm = _tfmm()
+    x = complex_gaussian(case["n_rwg"], 11)
+    xd = torch.from_numpy(x.astype(np.complex64)).cuda()
+    spec = torch.full((1, case["G"], 2, case["nt"] * case["npf"]), float("nan"), dtype=torch.complex64, device="cuda")
+    tfmm.tfmm_aggregate(case["plan"], xd, spec)
+    torch.cuda.synchronize()
+    got = spec.cpu().numpy()[0]
+    ref = apply.aggregate_all(case["T"], case["members"], x)
+    assert np.isfinite(got).all()
+    for g in range(case["G"]):
+        for a in range(2):
+            assert _rel(got[g, a], ref[g, a]) <= TOL, (g, a, _rel(got[g, a], ref[g, a]))
+
+
+@pytest.mark.parametrize("weights,beta", [(True, 0.0), (False, 0.0), (True, 0.5 - 0.25j)])
+def test_disaggregate_matches_oracle(case, weights, beta):
+    tfmm = _tfmm()
+    G, nd = case["G"], case["nt"] * case["npf"]
+    g_in = complex_gaussian((G, 2, nd), 12)
+    y0 = complex_gaussian(case["n_rwg"], 13)
+    gd = torch.from_numpy(g_in.astype(np.complex64)).cuda().reshape(1, G, 2, nd)
+    yd = torch.from_numpy(y0.astype(np.complex64)).cuda()
+    tfmm.tfmm_disaggregate(case["plan"], gd, yd, apply_weights=weights, beta=beta)
+    torch.cuda.synchronize()
+    got = yd.cpu().numpy()
+    ref = apply.disaggregate_all(case["T"], case["members"], g_in, case["n_rwg"],
+                                 case["w"] if weights else None, beta=beta, y0=y0)
+    for g, ids in enumerate(case["members"]):
+        assert _rel(got[ids], ref[ids]) <= TOL, (g, _rel(got[ids], ref[ids]))
+
+
+def test_multi_rhs_and_leading_dimension(case):
+    tfmm = _tfmm()
+    R, n = 3, case["n_rwg"]
+    ld = n + 5
+    X = complex_gaussian((R, ld), 21)
+    xd = torch.from_numpy(X.astype(np.complex64)).cuda()
+    spec = torch.empty((R, case["G"], 2, case["nt"] * case["npf"]), dtype=torch.complex64, device="cuda")
+    tfmm.tfmm_aggregate(case["plan"], xd, spec, R=R, ldx=ld)
+    yd = torch.zeros((R, ld), dtype=torch.complex64, device="cuda")
+    tfmm.tfmm_disaggregate(case["plan"], spec, yd, R=R, ldy=ld)
+    torch.cuda.synchronize()
+    S = spec.cpu().numpy()
+    Y = yd.cpu().numpy()
+    for r in range(R):
+        ref = apply.aggregate_all(case["T"], case["members"], X[r, :n])
+        assert _rel(S[r], ref) <= TOL
+        refy = apply.disaggregate_all(case["T"], case["members"], S[r].astype(np.complex128), n, case["w"])
+        assert _rel(Y[r, :n], refy) <= TOL
+        assert np.all(Y[r, n:] == 0)  # padding rows untouched
+
+
+def test_repeated_launches_reuse_the_work_queue(case):
+    """The self-resetting queue: identical results over many back-to-back launches."""
+    tfmm = _tfmm()
+    x = complex_gaussian(case["n_rwg"], 31)
+    xd = torch.from_numpy(x.astype(np.complex64)).cuda()
+    spec = torch.empty((1, case["G"], 2, case["nt"] * case["npf"]), dtype=torch.complex64, device="cuda")
+    tfmm.tfmm_aggregate(case["plan"], xd, spec)
+    first = spec.clone()
+    for _ in range(20):
+        tfmm.tfmm_aggregate(case["plan"], xd, spec)
+    torch.cuda.synchronize()
+    assert torch.equal(first, spec)
+
+
+def test_adjointness_on_gpu_outputs(case):
+    tfmm = _tfmm()
+    G, nd, n = case["G"], case["nt"] * case["npf"], case["n_rwg"]
+    x = complex_gaussian(n, 41)
+    g_in = complex_gaussian((G, 2, nd), 42)
+    xd = torch.from_numpy(x.astype(np.complex64)).cuda()
+    spec = torch.empty((1, G, 2, nd), dtype=torch.complex64, device="cuda")
+    tfmm.tfmm_aggregate(case["plan"], xd, spec)
+    yd = torch.zeros(n, dtype=torch.complex64, device="cuda")
+    gd = torch.from_numpy(g_in.astype(np.complex64)).cuda().reshape(1, G, 2, nd)
+    tfmm.tfmm_disaggregate(case["plan"], gd, yd)
+    torch.cuda.synchronize()
+    F = spec.cpu().numpy()[0].astype(np.complex128)
+    y = yd.cpu().numpy().astype(np.complex128)
+    lhs = np.vdot(case["w"][None, None, :] * g_in, F)
+    rhs = np.vdot(y, x)
+    assert abs(lhs - rhs) <= 1e-5 * np.linalg.norm(F) * np.linalg.norm(case["w"][None, None, :] * g_in)
+
+
+def test_dense_kernels_match_oracle(case):
+    tfmm = _tfmm()
+    tensors = [[hosvd.reconstruct(t) for t in per] for per in case["T"]]
+    tfmm.tfmm_plan_set_dense(case["plan"], tensors)
+    G, nd, n = case["G"], case["nt"] * case["npf"], case["n_rwg"]
+    x = complex_gaussian(n, 51)
+    xd = torch.from_numpy(x.astype(np.complex64)).cuda()
+    spec = torch.empty((1, G, 2, nd), dtype=torch.complex64, device="cuda")
+    tfmm.tfmm_aggregate_dense(case["plan"], xd, spec)
+    yd = torch.zeros(n, dtype=torch.complex64, device="cuda")
+    tfmm.tfmm_disaggregate_dense(case["plan"], spec, yd)
+    torch.cuda.synchronize()
+    F = spec.cpu().numpy()[0]
+    ref = apply.aggregate_all(tensors, case["members"], x, tucker=False)
+    assert _rel(F, ref) <= TOL
+    refy = apply.disaggregate_all(tensors, case["members"], F.astype(np.complex128), n, case["w"], tucker=False)
+    assert _rel(yd.cpu().numpy(), refy) <= TOL
+
+
+def test_host_matvec_equals_device_path(case):
+    tfmm = _tfmm()
+    n = case["n_rwg"]
+    x = complex_gaussian(n, 61).astype(np.complex64)
+    y = np.zeros(n, np.complex64)
+    tfmm.tfmm_matvec_host(case["plan"], x, y)
+    xd = torch.from_numpy(x).cuda()
+    spec = torch.empty((1, case["G"], 2, case["nt"] * case["npf"]), dtype=torch.complex64, device="cuda")
+    tfmm.tfmm_aggregate(case["plan"], xd, spec)
+    yd = torch.zeros(n, dtype=torch.complex64, device="cuda")
+    tfmm.tfmm_disaggregate(case["plan"], spec, yd)
+    torch.cuda.synchronize()
+    assert np.array_equal(y, yd.cpu().numpy())
+
+
+def test_hot_path_argument_errors(case):
+    tfmm = _tfmm()
+    n = case["n_rwg"]
+    xd = torch.zeros(n, dtype=torch.complex64, device="cuda")
+    spec = torch.empty((8, case["G"], 2, case["nt"] * case["npf"]), dtype=torch.complex64, device="cuda")
+    with pytest.raises(tfmm.TfmmError) as e:
+        tfmm.tfmm_aggregate(case["plan"], xd, spec, R=5)  # > max_rhs
+    assert e.value.status == tfmm.INVALID_ARG
+    with pytest.raises(tfmm.TfmmError) as e:
+        tfmm.tfmm_aggregate(case["plan"], xd, spec, R=1, ldx=n - 1)
+    assert e.value.status == tfmm.INVALID_ARG
+
+
+def test_from_tucker_rejects_bad_ranks():
+    tfmm = _tfmm()
+    n_rwg, members, T, factors = _case(3, 4, 8, [5], lambda rng, nb: [(2, 2, 2), (2, 2, 2)])
+    Ut, Up, Ub, C = factors[0][0]
+    bad = [[(Ut, Up, Ub, np.zeros((2, 2, 9), complex)), factors[0][1]]]  # r_beta 9 > n_beta 5
+    with pytest.raises(tfmm.TfmmError) as e:
+        tfmm.tfmm_plan_from_tucker(n_rwg, 4, 8, members, bad)
+    assert e.value.status == tfmm.INVALID_ARG
+    with pytest.raises(tfmm.TfmmError):
+        tfmm.tfmm_plan_from_tucker(n_rwg, 4, 8, [np.array([0, 0, 1, 2, 3])], factors)  # repeated id
