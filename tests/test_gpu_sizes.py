@@ -1,0 +1,125 @@
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py times.
+
+The library builds the whole plan (30-lambda sphere: 972,000 RWGs, 2-lambda boxes,
+6 digits, gamma = 1e-6; and the 10-lambda sphere with the plane-wave + Gaussian
+right-hand side).  The oracle cannot build every group in seconds, so it builds
+a sample of groups from the same mesh (its own RWGs, grouping, far-fields by
+Eq. 4) and checks the GPU outputs of those groups:
+
+* aggregation:   ||F_gpu - A x||   <= gamma ||A||_F ||x_g|| + 1e-5 ||A x||
+  (Tucker truncation bound + FP32), per group and component;
+* disaggregation of a seeded spectra input, same bound with A^H W;
+* properties at any size: weighted adjointness of the GPU outputs.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import apply, planewave
+from paper_2103_05822_gb300.inputs import WORKLOADS, complex_gaussian, icosphere
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _build(name):
+    from paper_2103_05822_gb300 import tfmm
+    w = WORKLOADS[name]
+    v, f = icosphere(w.diameter, w.nu)
+    mesh = tfmm.tfmm_mesh_create(v, f)
+    prm = tfmm.tfmm_params_default(k=2 * math.pi, box=w.box, digits=float(w.digits), tol=w.tol, max_rhs=1)
+    plan = tfmm.tfmm_plan_create(mesh, prm)
+    P = oracle.problem.build(v, f, k=2 * math.pi, box=w.box, digits=w.digits, tol=w.tol,
+                             compress=False, keep_tensors=False)
+    return w, v, f, plan, P
+
+
+def _sample(P, count=3):
+    G = P.groups.n_groups
+    sizes = np.array([len(m) for m in P.groups.members])
+    # the largest group, the smallest and one of median size
+    return sorted({int(np.argmax(sizes)), int(np.argmin(sizes)), int(np.argsort(sizes)[G // 2])})[:count]
+
+
+@pytest.fixture(scope="module", params=["sphere30", "sphere10"])
+def full(request):
+    return _build(request.param)
+
+
+def test_fullsize_groups_identical(full):
+    from paper_2103_05822_gb300 import tfmm
+    w, v, f, plan, P = full
+    info = plan.info
+    assert info["n_rwg"] == w.n_rwg and info["n_groups"] == P.groups.n_groups
+    assert info["L"] == P.grid.L
+    members = tfmm.tfmm_plan_members(plan)
+    for g in _sample(P):
+        assert np.array_equal(members[g], P.groups.members[g])
+
+
+def test_fullsize_aggregate_sampled_groups(full):
+    from paper_2103_05822_gb300 import tfmm
+    w, v, f, plan, P = full
+    info = plan.info
+    x = complex_gaussian(w.n_rwg, w.seed)
+    if w.rhs == "planewave+gaussian":
+        k_inc, th, _ = planewave.incidence(0.0, 0.0)  # theta_inc = 0, x-polarised
+        Vd = torch.empty((1, w.n_rwg), dtype=torch.complex64, device="cuda")
+        tfmm.tfmm_planewave(plan, k_inc[None], th[None], Vd)
+        xg = Vd[0] + torch.from_numpy(x.astype(np.complex64)).cuda()
+        x_or = planewave.planewave_rhs(v, P.rwg, P.k, k_inc, th) + x
+    else:
+        xg = torch.from_numpy(x.astype(np.complex64)).cuda()
+        x_or = x
+    spec = torch.empty((1, info["n_groups"], 2, info["n_dir"]), dtype=torch.complex64, device="cuda")
+    tfmm.tfmm_aggregate(plan, xg, spec)
+    torch.cuda.synchronize()
+    got = spec.cpu().numpy()[0]
+    assert np.isfinite(got).all()
+    for g in _sample(P):
+        A = P.group_tensors(g)
+        ids = P.groups.members[g]
+        for a in range(2):
+            ref = apply.dense_aggregate(A[a], x_or[ids]).reshape(-1)
+            bound = w.tol * np.linalg.norm(A[a]) * np.linalg.norm(x_or[ids]) + 1e-5 * np.linalg.norm(ref)
+            assert np.linalg.norm(got[g, a] - ref) <= bound, (g, a)
+
+
+def test_fullsize_disaggregate_sampled_groups(full):
+    from paper_2103_05822_gb300 import tfmm
+    w, v, f, plan, P = full
+    info = plan.info
+    gin = complex_gaussian((info["n_groups"], 2, info["n_dir"]), w.seed + 100)
+    gd = torch.from_numpy(gin.astype(np.complex64)).cuda().reshape(1, info["n_groups"], 2, info["n_dir"])
+    y = torch.zeros(w.n_rwg, dtype=torch.complex64, device="cuda")
+    tfmm.tfmm_disaggregate(plan, gd, y)
+    torch.cuda.synchronize()
+    got = y.cpu().numpy()
+    for g in _sample(P):
+        A = P.group_tensors(g)
+        ids = P.groups.members[g]
+        ref = sum(apply.dense_disaggregate(A[a], gin[g, a], P.grid.weights) for a in range(2))
+        bound = sum(w.tol * np.linalg.norm(A[a]) * np.linalg.norm(P.grid.weights * gin[g, a]) for a in range(2))
+        assert np.linalg.norm(got[ids] - ref) <= bound + 1e-5 * np.linalg.norm(ref), g
+
+
+def test_fullsize_adjointness(full):
+    from paper_2103_05822_gb300 import tfmm
+    w, v, f, plan, P = full
+    info = plan.info
+    x = complex_gaussian(w.n_rwg, 5)
+    gin = complex_gaussian((info["n_groups"], 2, info["n_dir"]), 6)
+    xd = torch.from_numpy(x.astype(np.complex64)).cuda()
+    spec = torch.empty((1, info["n_groups"], 2, info["n_dir"]), dtype=torch.complex64, device="cuda")
+    tfmm.tfmm_aggregate(plan, xd, spec)
+    gd = torch.from_numpy(gin.astype(np.complex64)).cuda().reshape(spec.shape)
+    y = torch.zeros(w.n_rwg, dtype=torch.complex64, device="cuda")
+    tfmm.tfmm_disaggregate(plan, gd, y)
+    torch.cuda.synchronize()
+    F = spec.cpu().numpy()[0].astype(np.complex128)
+    Wg = P.grid.weights[None, None, :] * gin
+    lhs = np.vdot(Wg, F)
+    rhs = np.vdot(y.cpu().numpy().astype(np.complex128), x)
+    assert abs(lhs - rhs) <= 1e-5 * np.linalg.norm(Wg) * np.linalg.norm(F)
