@@ -508,7 +508,7 @@ Plan::~Plan() {
     F(d_grp_rwg); F(d_weights); F(d_counters); F(d_factors); F(d_items); F(d_agg_order); F(d_dis_order);
     F(d_dense); F(d_dense_items); F(d_dense_agg_order); F(d_dense_dis_order); F(d_geom);
     F(d_ws_x); F(d_ws_spec); F(d_ws_y);
-    for (auto& f : f64) F(f.base);
+    for (auto* a : f64_arenas) F(a);
 }
 
 void pack_factors_fp32(Plan& P, cudaStream_t s) {

@@ -78,7 +78,7 @@ struct Schedule {
 };
 
 // ----------------------------------------------------------------------- plan
-struct HostFactors64 {     // FP64 factors of one (g, alpha), device memory
+struct HostFactors64 {     // FP64 factors of one (g, alpha), device memory (inside an arena)
     double2* base = nullptr;  // U_theta | U_phi | U_beta | core (column-major, back to back)
     int rt = 0, rp = 0, rb = 0;
 };
@@ -127,7 +127,8 @@ struct Plan {
     RwgGeom* d_geom = nullptr;         // N, global RWG order
     std::vector<RwgGeom> geom;
     // FP64 factors (exports)
-    std::vector<HostFactors64> f64;    // G x 2
+    std::vector<HostFactors64> f64;    // G x 2, pointers into f64_arenas
+    std::vector<double2*> f64_arenas;  // owned device allocations
     // workspace of tfmm_matvec_host
     int ws_R = 0;
     float2 *d_ws_x = nullptr, *d_ws_spec = nullptr, *d_ws_y = nullptr;

@@ -23,6 +23,10 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <cstdio>
+#include <exception>
+#include <memory>
+#include <thread>
 
 #include "internal.h"
 
@@ -298,9 +302,11 @@ double ms_since(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
-// Smallest r >= 1 whose discarded eigenvalues (ascending list, clamped at 0) sum to <= thr2.
-int choose_rank(const double* ev, int n, double thr2) {
-    double tail = 0.0;
+// Smallest r >= 1 whose discarded eigenvalues (ascending list, clamped at 0) sum to <= thr2;
+// tail0 is energy already discarded outside the list.
+int choose_rank(const double* ev, int n, double thr2, double tail0 = 0.0) {
+    double tail = tail0;
+    if (tail > thr2) return std::max(n, 1);
     int r = n;
     for (int i = 0; i < n; ++i) {  // discard i+1 smallest
         tail += std::max(ev[i], 0.0);
@@ -314,14 +320,177 @@ int choose_rank(const double* ev, int n, double thr2) {
 
 // Batched Hermitian eigen-decomposition of `count` n x n matrices (lower part
 // valid, ld n, stride n*n) with eigenvalues ascending in W (count x n).
-// Uses the batched solver when the library accepts the size, else one Xsyevd per
+// Cyclic Jacobi eigen-decomposition of small Hermitian matrices, one CTA per
+// matrix, the matrix in shared memory (Golub & Van Loan, "Matrix
+// Computations", Sec. 8.5: symmetric Schur rotations, parallel round-robin
+// ordering; the complex Hermitian case first removes the phase of a_pq).
+// G: count x n x n, lower triangle valid on entry; on exit the eigenvectors
+// (columns, ascending eigenvalues) overwrite G and W holds the eigenvalues.
+constexpr int kJacobiMax = 112;
+constexpr int kJacobiThreads = 512;
+constexpr int kJacobiSweeps = 20;
+
+__global__ void __launch_bounds__(kJacobiThreads) jacobi_eig_kernel(double2* G, double* W, int n) {
+    extern __shared__ double2 sA[];  // n x ld, column-major, ld odd (no bank conflicts on rows)
+    __shared__ double s_c[kJacobiMax / 2 + 1], s_s[kJacobiMax / 2 + 1];
+    __shared__ double2 s_e[kJacobiMax / 2 + 1];
+    __shared__ int s_p[kJacobiMax / 2 + 1], s_q[kJacobiMax / 2 + 1];
+    __shared__ double s_red[2][kJacobiThreads / 32];
+    __shared__ double s_d[kJacobiMax];
+    const int ld = n | 1, tid = threadIdx.x, NT = blockDim.x;
+    double2* V = G + (int64_t)blockIdx.x * n * n;
+    double* Wb = W + (int64_t)blockIdx.x * n;
+    for (int e = tid; e < n * n; e += NT) {
+        const int i = e % n, j = e / n;
+        double2 v;
+        if (i > j) {
+            v = V[i + (int64_t)n * j];
+        } else if (i < j) {
+            v = V[j + (int64_t)n * i];
+            v.y = -v.y;
+        } else {
+            v = make_double2(V[i + (int64_t)n * i].x, 0.0);
+        }
+        sA[i + ld * j] = v;
+    }
+    __syncthreads();
+    for (int e = tid; e < n * n; e += NT) V[e] = make_double2((e % n) == (e / n) ? 1.0 : 0.0, 0.0);
+    __syncthreads();
+    const int m = n + (n & 1);  // even number of players (one dummy when n is odd)
+    const int half = m / 2;
+    for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
+        // convergence: off-diagonal energy against the total
+        double off = 0.0, tot = 0.0;
+        for (int e = tid; e < n * n; e += NT) {
+            const int i = e % n, j = e / n;
+            const double2 v = sA[i + ld * j];
+            const double a2 = v.x * v.x + v.y * v.y;
+            tot += a2;
+            if (i != j) off += a2;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_xor_sync(0xffffffffu, off, o);
+            tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        }
+        if ((tid & 31) == 0) {
+            s_red[0][tid >> 5] = off;
+            s_red[1][tid >> 5] = tot;
+        }
+        __syncthreads();
+        off = 0.0;
+        tot = 0.0;
+        for (int w = 0; w < NT / 32; ++w) {
+            off += s_red[0][w];
+            tot += s_red[1][w];
+        }
+        __syncthreads();
+        if (!(off > 1e-28 * tot)) break;  // also stops on an all-zero matrix
+        for (int step = 0; step < m - 1; ++step) {
+            if (tid < half) {
+                const int pa = tid, pb = m - 1 - tid;
+                const int a = pa == 0 ? 0 : 1 + (pa - 1 + step) % (m - 1);
+                const int b = pb == 0 ? 0 : 1 + (pb - 1 + step) % (m - 1);
+                const int p = min(a, b), q = max(a, b);
+                double c = 1.0, sn = 0.0;
+                double2 ph = make_double2(1.0, 0.0);
+                if (q < n) {
+                    const double2 apq = sA[p + ld * q];
+                    const double r = hypot(apq.x, apq.y);
+                    if (r > 0.0) {
+                        const double app = sA[p + ld * p].x, aqq = sA[q + ld * q].x;
+                        const double tau = (aqq - app) / (2.0 * r);
+                        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                        c = 1.0 / sqrt(1.0 + t * t);
+                        sn = t * c;
+                        ph = make_double2(apq.x / r, -apq.y / r);  // e^{-i phi}, a_pq = r e^{i phi}
+                    }
+                }
+                s_p[tid] = p;
+                s_q[tid] = q < n ? q : -1;
+                s_c[tid] = c;
+                s_s[tid] = sn;
+                s_e[tid] = ph;
+            }
+            __syncthreads();
+            // A <- A Q and V <- V Q, Q = [[c, s], [-s e, c e]] on columns (p, q), e = e^{-i phi}
+            for (int e = tid; e < half * n; e += NT) {
+                const int k = e / n, i = e % n;
+                const int q = s_q[k];
+                if (q < 0) continue;
+                const int p = s_p[k];
+                const double c = s_c[k], sn = s_s[k];
+                const double2 ph = s_e[k];
+                const double2 qqp = make_double2(-sn * ph.x, -sn * ph.y), qqq = make_double2(c * ph.x, c * ph.y);
+                const double2 x = sA[i + ld * p], y = sA[i + ld * q];
+                sA[i + ld * p] = make_double2(c * x.x + qqp.x * y.x - qqp.y * y.y, c * x.y + qqp.x * y.y + qqp.y * y.x);
+                sA[i + ld * q] = make_double2(sn * x.x + qqq.x * y.x - qqq.y * y.y, sn * x.y + qqq.x * y.y + qqq.y * y.x);
+                const double2 vx = V[i + (int64_t)n * p], vy = V[i + (int64_t)n * q];
+                V[i + (int64_t)n * p] =
+                    make_double2(c * vx.x + qqp.x * vy.x - qqp.y * vy.y, c * vx.y + qqp.x * vy.y + qqp.y * vy.x);
+                V[i + (int64_t)n * q] =
+                    make_double2(sn * vx.x + qqq.x * vy.x - qqq.y * vy.y, sn * vx.y + qqq.x * vy.y + qqq.y * vy.x);
+            }
+            __syncthreads();
+            // A <- Q^H A on rows (p, q)
+            for (int e = tid; e < half * n; e += NT) {
+                const int k = e / n, j = e % n;
+                const int q = s_q[k];
+                if (q < 0) continue;
+                const int p = s_p[k];
+                const double c = s_c[k], sn = s_s[k];
+                const double2 ph = s_e[k];
+                // conj(Q_qp) = -s conj(e), conj(Q_qq) = c conj(e)
+                const double2 cqp = make_double2(-sn * ph.x, sn * ph.y), cqq = make_double2(c * ph.x, -c * ph.y);
+                const double2 x = sA[p + ld * j], y = sA[q + ld * j];
+                sA[p + ld * j] = make_double2(c * x.x + cqp.x * y.x - cqp.y * y.y, c * x.y + cqp.x * y.y + cqp.y * y.x);
+                sA[q + ld * j] = make_double2(sn * x.x + cqq.x * y.x - cqq.y * y.y, sn * x.y + cqq.x * y.y + cqq.y * y.x);
+            }
+            __syncthreads();
+            // the rotated pair is diagonal up to rounding: make it exact
+            if (tid < half && s_q[tid] >= 0) {
+                const int p = s_p[tid], q = s_q[tid];
+                sA[p + ld * q] = make_double2(0.0, 0.0);
+                sA[q + ld * p] = make_double2(0.0, 0.0);
+                sA[p + ld * p].y = 0.0;
+                sA[q + ld * q].y = 0.0;
+            }
+            __syncthreads();
+        }
+    }
+    // eigenvalues ascending (ties by index), eigenvector columns permuted alike
+    for (int i = tid; i < n; i += NT) s_d[i] = sA[i + ld * i].x;
+    __syncthreads();
+    for (int e = tid; e < n * n; e += NT) {
+        const int i = e % n, j = e / n;
+        int rank = 0;
+        const double dj = s_d[j];
+        for (int k = 0; k < n; ++k) rank += (s_d[k] < dj) || (s_d[k] == dj && k < j);
+        sA[i + ld * rank] = V[i + (int64_t)n * j];
+        if (i == 0) Wb[rank] = dj;
+    }
+    __syncthreads();
+    for (int e = tid; e < n * n; e += NT) V[e] = sA[(e % n) + ld * (e / n)];
+}
+
+// Small matrices (n <= kJacobiMax): the Jacobi kernel above (TFMM_EIG=cusolver
+// disables it).  Otherwise the batched cuSOLVER solver when the library accepts the size, else one Xsyevd per
 // matrix (TFMM_EIG=single forces the latter).
 void eig_batched(cusolverDnHandle_t sol, cusolverDnParams_t prm, double2* A, double* W, int n, int count,
                  cudaStream_t s) {
     if (count == 0) return;
+    const char* env = std::getenv("TFMM_EIG");
+    if (n <= kJacobiMax && !(env && std::strcmp(env, "cusolver") == 0)) {
+        const size_t smem = sizeof(double2) * (size_t)n * (size_t)(n | 1);
+        if (smem > 48 * 1024)
+            TFMM_CUDA_CHECK(cudaFuncSetAttribute(jacobi_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem));
+        jacobi_eig_kernel<<<count, kJacobiThreads, smem, s>>>(A, W, n);
+        TFMM_CUDA_CHECK(cudaGetLastError());
+        TFMM_CUDA_CHECK(cudaStreamSynchronize(s));
+        return;
+    }
     size_t dbytes = 0, hbytes = 0;
     DevBuf info(sizeof(int) * count);
-    const char* env = std::getenv("TFMM_EIG");
     const bool force_single = env && std::strcmp(env, "single") == 0;
     cusolverStatus_t st = CUSOLVER_STATUS_NOT_SUPPORTED;
     if (!force_single)
@@ -350,12 +519,410 @@ void eig_batched(cusolverDnHandle_t sol, cusolverDnParams_t prm, double2* A, dou
         if (hinfo[i] != 0) fail(TFMM_NUMERIC, "eigen-decomposition failed (info " + std::to_string(hinfo[i]) + ")");
 }
 
+// out[e] = sum over parts of part[j][e] (FP64 complex), e < count
+__global__ void sum_parts_kernel(const double2* __restrict__ part, int nparts, int64_t count, double2* __restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int j = 0; j < nparts; ++j) {
+            const double2 v = part[(int64_t)j * count + e];
+            acc.x += v.x;
+            acc.y += v.y;
+        }
+        out[e] = acc;
+    }
+}
+
+struct Worker {  // one host thread's stream and library handles for per-tensor setup work
+    cudaStream_t s = nullptr;
+    cublasHandle_t blas = nullptr;
+    cusolverDnHandle_t sol = nullptr;
+    cusolverDnParams_t prm = nullptr;
+    Worker() {
+        TFMM_CUDA_CHECK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        CUBLAS_CHECK(cublasCreate(&blas));
+        CUBLAS_CHECK(cublasSetStream(blas, s));
+        CUSOLVER_CHECK(cusolverDnCreate(&sol));
+        CUSOLVER_CHECK(cusolverDnSetStream(sol, s));
+        CUSOLVER_CHECK(cusolverDnCreateParams(&prm));
+    }
+    ~Worker() {
+        if (prm) cusolverDnDestroyParams(prm);
+        if (sol) cusolverDnDestroy(sol);
+        if (blas) cublasDestroy(blas);
+        if (s) cudaStreamDestroy(s);
+    }
+    Worker(const Worker&) = delete;
+    Worker& operator=(const Worker&) = delete;
+};
+
+struct Timers {
+    double mode1 = 0, mode2 = 0, gram3 = 0, eig3 = 0, fac3 = 0;
+};
+
+// Runs f(worker, i) for i in [0, n) on the worker threads (round robin), each
+// thread on the caller's device; rethrows the first failure.
+template <class F>
+void parallel_for(std::vector<std::unique_ptr<Worker>>& pool, int n, F&& f) {
+    int dev = 0;
+    TFMM_CUDA_CHECK(cudaGetDevice(&dev));
+    const int nw = (int)pool.size();
+    std::vector<std::exception_ptr> errs(nw);
+    std::vector<std::thread> th;
+    for (int w = 0; w < nw; ++w)
+        th.emplace_back([&, w] {
+            try {
+                TFMM_CUDA_CHECK(cudaSetDevice(dev));
+                for (int i = w; i < n; i += nw) f(*pool[w], w, i);
+                TFMM_CUDA_CHECK(cudaStreamSynchronize(pool[w]->s));
+            } catch (...) {
+                errs[w] = std::current_exception();
+            }
+        });
+    for (auto& t : th) t.join();
+    for (auto& e : errs)
+        if (e) std::rethrow_exception(e);
+}
+
+// One Hermitian eigen-decomposition (lower part valid, in place, eigenvalues ascending).
+void eig_one(Worker& w, double2* A, double* W, int n, int* info) {
+    size_t dbytes = 0, hbytes = 0;
+    CUSOLVER_CHECK(cusolverDnXsyevd_bufferSize(w.sol, w.prm, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n,
+                                               CUDA_C_64F, A, n, CUDA_R_64F, W, CUDA_C_64F, &dbytes, &hbytes));
+    DevBuf work(std::max<size_t>(dbytes, 16));
+    std::vector<char> hwork(std::max<size_t>(hbytes, 16));
+    CUSOLVER_CHECK(cusolverDnXsyevd(w.sol, w.prm, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, CUDA_C_64F, A,
+                                    n, CUDA_R_64F, W, CUDA_C_64F, work.p, dbytes, hwork.data(), hbytes, info));
+    int h = 0;
+    TFMM_CUDA_CHECK(cudaMemcpyAsync(&h, info, sizeof(int), cudaMemcpyDeviceToHost, w.s));
+    TFMM_CUDA_CHECK(cudaStreamSynchronize(w.s));  // the workspaces above are released on return
+    if (h != 0) fail(TFMM_NUMERIC, "eigen-decomposition failed (info " + std::to_string(h) + ")");
+}
+
+constexpr int kGramParts = 64;
+
+// Gram matrix of a short, wide operand by split-K: the long dimension is cut
+// into chunks, one strided-batched ZGEMM forms a partial Gram per chunk and a
+// reduction sums them (cuBLAS ZHERK parallelises such shapes poorly).
+//   rows = true : G = A A^H, A is n x k column-major (ld lda)
+//   rows = false: G = A^H A, A is k x n column-major (ld lda)
+// part: scratch of at least (kGramParts + 1) n^2 elements.  G is n x n, both triangles.
+void gram_splitk(Worker& w, bool rows, int n, int64_t k, const double2* A, int64_t lda, double2* G, double2* part) {
+    const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0), zero = make_cuDoubleComplex(0.0, 0.0);
+    const int64_t kc = std::max<int64_t>(128, (k + kGramParts - 1) / kGramParts);
+    const int nfull = (int)(k / kc);
+    const int64_t krem = k - (int64_t)nfull * kc;
+    const int64_t nn = (int64_t)n * n;
+    const cublasOperation_t oa = rows ? CUBLAS_OP_N : CUBLAS_OP_C, ob = rows ? CUBLAS_OP_C : CUBLAS_OP_N;
+    const int64_t stride = rows ? lda * kc : kc;
+    if (nfull > 0)
+        CUBLAS_CHECK(cublasZgemmStridedBatched(w.blas, oa, ob, n, n, (int)kc, &one, (const cuDoubleComplex*)A, (int)lda,
+                                               stride, (const cuDoubleComplex*)A, (int)lda, stride, &zero,
+                                               (cuDoubleComplex*)part, n, nn, nfull));
+    int nparts = nfull;
+    if (krem > 0) {
+        const double2* Ar = A + (rows ? lda * kc * nfull : kc * nfull);
+        CUBLAS_CHECK(cublasZgemm(w.blas, oa, ob, n, n, (int)krem, &one, (const cuDoubleComplex*)Ar, (int)lda,
+                                 (const cuDoubleComplex*)Ar, (int)lda, &zero, (cuDoubleComplex*)(part + nn * nfull),
+                                 n));
+        ++nparts;
+    }
+    sum_parts_kernel<<<grid1d(nn), 256, 0, w.s>>>(part, nparts, nn, G);
+    TFMM_CUDA_CHECK(cudaGetLastError());
+}
+
 struct Tensor {      // one (group, alpha) tensor of the current batch
     int g, alpha, nb;
     double2* A;      // n_theta x n_phi x nb
-    double norm2 = 0;
+    double norm2 = 0;  // ||A||_F^2
+    double z2 = 0;     // energy left after the theta and phi projections
     int rt = 0, rp = 0, rb = 0;
 };
+
+// Sequentially truncated HOSVD of every tensor of a batch (modes theta, phi, beta).
+void hosvd_batch(Plan& P, std::vector<Tensor>& T, std::vector<std::unique_ptr<Worker>>& pool, cudaStream_t s,
+                 Timers& tm) {
+    (void)s;
+    const int nt = P.n_theta, np = P.n_phi;
+    const int nT = (int)T.size();
+    const int nw = (int)pool.size();
+    const double tol2 = P.params.tol * P.params.tol / 3.0;
+    const double r_one = 1.0, r_zero = 0.0;
+    const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0), zero = make_cuDoubleComplex(0.0, 0.0);
+    const char* env = std::getenv("TFMM_EIG");
+    const bool batched_small = !(env && std::strcmp(env, "single") == 0);
+    auto t0 = std::chrono::steady_clock::now();
+    std::vector<DevBuf> winfo(nw);
+    for (auto& b : winfo) b.alloc(sizeof(int));
+
+    // mode theta: G1 = A_(1) A_(1)^H (n_theta x n_theta)
+    DevBuf d_G1(sizeof(double2) * nT * nt * nt), d_W1(sizeof(double) * nT * nt);
+    const int ngmax = std::max(nt, np);
+    std::vector<DevBuf> wpart(nw);
+    for (auto& b : wpart) b.alloc(sizeof(double2) * (int64_t)(kGramParts + 1) * ngmax * ngmax);
+    parallel_for(pool, nT, [&](Worker& w, int wi, int t) {
+        gram_splitk(w, true, nt, (int64_t)np * T[t].nb, T[t].A, nt, d_G1.as<double2>() + (int64_t)t * nt * nt,
+                    wpart[wi].as<double2>());
+        if (!batched_small)
+            eig_one(w, d_G1.as<double2>() + (int64_t)t * nt * nt, d_W1.as<double>() + (int64_t)t * nt, nt,
+                    winfo[wi].as<int>());
+    });
+    if (batched_small) {
+        Worker& w0 = *pool[0];
+        eig_batched(w0.sol, w0.prm, d_G1.as<double2>(), d_W1.as<double>(), nt, nT, w0.s);
+    }
+    std::vector<double> W1((size_t)nT * nt);
+    TFMM_CUDA_CHECK(cudaMemcpy(W1.data(), d_W1.p, sizeof(double) * W1.size(), cudaMemcpyDeviceToHost));
+    int64_t y1_tot = 0;
+    std::vector<int64_t> y1_off(nT);
+    for (int t = 0; t < nT; ++t) {
+        double n2 = 0;
+        for (int i = 0; i < nt; ++i) n2 += std::max(W1[(size_t)t * nt + i], 0.0);
+        T[t].norm2 = n2;
+        T[t].rt = choose_rank(&W1[(size_t)t * nt], nt, tol2 * n2);
+        y1_off[t] = y1_tot;
+        y1_tot += (int64_t)T[t].rt * np * T[t].nb;
+    }
+    tm.mode1 += ms_since(t0);
+    t0 = std::chrono::steady_clock::now();
+
+    // U_theta; A1 = U_theta^H A_(1) -> [a, i_phi, n]; Y1 = [a, n, i_phi]; G2' = Y1^H Y1
+    int maxnb = 1;
+    for (int t = 0; t < nT; ++t) maxnb = std::max(maxnb, T[t].nb);
+    DevBuf d_Ut(sizeof(double2) * nT * nt * nt), d_Y1(sizeof(double2) * std::max<int64_t>(y1_tot, 1));
+    DevBuf d_G2(sizeof(double2) * nT * np * np), d_W2(sizeof(double) * nT * np);
+    std::vector<DevBuf> wA(nw);
+    for (auto& b : wA) b.alloc(sizeof(double2) * (int64_t)nt * np * maxnb);
+    parallel_for(pool, nT, [&](Worker& w, int wi, int t) {
+        const int rt = T[t].rt, nb = T[t].nb;
+        double2* Ut = d_Ut.as<double2>() + (int64_t)t * nt * nt;
+        take_top_kernel<<<grid1d((int64_t)nt * rt), 256, 0, w.s>>>(d_G1.as<double2>() + (int64_t)t * nt * nt, nt, nt,
+                                                                     nt - 1, rt, Ut, 0);
+        CUBLAS_CHECK(cublasZgemm(w.blas, CUBLAS_OP_C, CUBLAS_OP_N, rt, np * nb, nt, &one, (const cuDoubleComplex*)Ut, nt,
+                                 (const cuDoubleComplex*)T[t].A, nt, &zero, (cuDoubleComplex*)wA[wi].p, rt));
+        permute3_kernel<<<grid1d((int64_t)rt * np * nb), 256, 0, w.s>>>(wA[wi].as<double2>(),
+                                                                         d_Y1.as<double2>() + y1_off[t], rt, np, nb, 0);
+        TFMM_CUDA_CHECK(cudaGetLastError());
+        gram_splitk(w, false, np, (int64_t)rt * nb, d_Y1.as<double2>() + y1_off[t], (int64_t)rt * nb,
+                    d_G2.as<double2>() + (int64_t)t * np * np, wpart[wi].as<double2>());
+        if (!batched_small)
+            eig_one(w, d_G2.as<double2>() + (int64_t)t * np * np, d_W2.as<double>() + (int64_t)t * np, np,
+                    winfo[wi].as<int>());
+    });
+    if (batched_small) {
+        Worker& w0 = *pool[0];
+        eig_batched(w0.sol, w0.prm, d_G2.as<double2>(), d_W2.as<double>(), np, nT, w0.s);
+    }
+    std::vector<double> W2((size_t)nT * np);
+    TFMM_CUDA_CHECK(cudaMemcpy(W2.data(), d_W2.p, sizeof(double) * W2.size(), cudaMemcpyDeviceToHost));
+    int n3max = 1, mmax = 1;
+    for (int t = 0; t < nT; ++t) {
+        T[t].rp = choose_rank(&W2[(size_t)t * np], np, tol2 * T[t].norm2);
+        double z2 = 0.0;
+        for (int i = np - T[t].rp; i < np; ++i) z2 += std::max(W2[(size_t)t * np + i], 0.0);
+        T[t].z2 = z2;
+        mmax = std::max(mmax, T[t].rt * T[t].rp);
+        n3max = std::max(n3max, std::min(T[t].nb, T[t].rt * T[t].rp));
+    }
+    tm.mode2 += ms_since(t0);
+    t0 = std::chrono::steady_clock::now();
+    std::vector<DevBuf> wV(nw);
+    for (auto& b : wV) b.alloc(sizeof(double2) * (int64_t)std::max(np, mmax) * std::max(np, n3max));
+
+    // mode beta, in two passes over the batch.  Pass A (per tensor): Z = [n, a, b]
+    // (n_beta x m, m = r_t r_p), Gram of its smaller side, eigen-decomposition, rank.
+    // Then one allocation holds the batch's FP64 factors.  Pass B (per tensor):
+    // U_beta (QR-orthonormalised when taken from Z V), core C_(3) = U_beta^H Z.
+    int64_t z_tot = 0, g3_tot = 0;
+    std::vector<int64_t> z_off(nT), g3_off(nT);
+    for (int t = 0; t < nT; ++t) {
+        const int m = T[t].rt * T[t].rp, n = std::min(T[t].nb, m);
+        z_off[t] = z_tot;
+        z_tot += (int64_t)T[t].nb * m;
+        g3_off[t] = g3_tot;
+        g3_tot += (int64_t)n * n;
+    }
+    DevBuf d_Z(sizeof(double2) * std::max<int64_t>(z_tot, 1)), d_G3(sizeof(double2) * std::max<int64_t>(g3_tot, 1));
+    DevBuf d_W3(sizeof(double) * std::max<int64_t>((int64_t)nT * n3max, 1));
+    // eigen-solver workspace per worker, sized for the largest problem of the batch
+    // default: Xsyevdx, eigenvectors only for eigenvalues above (gamma^2/6 ||A||^2) / n, whose
+    // sum bounds what it leaves out by half the truncation budget; TFMM_EIG3=syevd: all of them
+    const char* e3 = std::getenv("TFMM_EIG3");
+    const bool use_dx = !(e3 && std::strcmp(e3, "syevd") == 0);
+    size_t eig_d = 16, eig_h = 16;
+    {
+        Worker& w0 = *pool[0];
+        for (int t = 0; t < nT; ++t) {
+            const int n = std::min(T[t].nb, T[t].rt * T[t].rp);
+            size_t db = 0, hb = 0;
+            CUSOLVER_CHECK(cusolverDnXsyevd_bufferSize(w0.sol, w0.prm, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
+                                                       n, CUDA_C_64F, d_G3.p, n, CUDA_R_64F, d_W3.p, CUDA_C_64F, &db,
+                                                       &hb));
+            eig_d = std::max(eig_d, db);
+            eig_h = std::max(eig_h, hb);
+            if (use_dx) {
+                double vl = 0.0, vu = 1.0;
+                int64_t meig = 0;
+                CUSOLVER_CHECK(cusolverDnXsyevdx_bufferSize(w0.sol, w0.prm, CUSOLVER_EIG_MODE_VECTOR,
+                                                            CUSOLVER_EIG_RANGE_V, CUBLAS_FILL_MODE_LOWER, n, CUDA_C_64F,
+                                                            d_G3.p, n, &vl, &vu, 0, 0, &meig, CUDA_R_64F, d_W3.p,
+                                                            CUDA_C_64F, &db, &hb));
+                eig_d = std::max(eig_d, db);
+                eig_h = std::max(eig_h, hb);
+            }
+        }
+    }
+    std::vector<DevBuf> weig(nw);
+    std::vector<std::vector<char>> weigh(nw);
+    for (int i = 0; i < nw; ++i) {
+        weig[i].alloc(eig_d);
+        weigh[i].resize(eig_h);
+    }
+    std::vector<double> ms_g(nw, 0.0), ms_e(nw, 0.0), ms_f(nw, 0.0);
+    std::vector<std::vector<double>> W3(nT);
+    std::vector<int> nvec(nT, 0);  // eigenvectors returned per tensor (ascending, first columns)
+    parallel_for(pool, nT, [&](Worker& w, int wi, int t) {
+        auto ta = std::chrono::steady_clock::now();
+        const int rt = T[t].rt, rp = T[t].rp, nb = T[t].nb, m = rt * rp, n = std::min(nb, m);
+        double2* Vp = wV[wi].as<double2>();
+        // V_r (n_phi x r_p) from the mode-2 Gram; A2 = Y1 V_r -> [a, n, b]; Z = [n, a, b]
+        take_top_kernel<<<grid1d((int64_t)np * rp), 256, 0, w.s>>>(d_G2.as<double2>() + (int64_t)t * np * np, np, np,
+                                                                     np - 1, rp, Vp, 0);
+        CUBLAS_CHECK(cublasZgemm(w.blas, CUBLAS_OP_N, CUBLAS_OP_N, rt * nb, rp, np, &one,
+                                 (const cuDoubleComplex*)(d_Y1.as<double2>() + y1_off[t]), rt * nb,
+                                 (const cuDoubleComplex*)Vp, np, &zero, (cuDoubleComplex*)wA[wi].p, rt * nb));
+        double2* Z = d_Z.as<double2>() + z_off[t];
+        permute3_kernel<<<grid1d((int64_t)rt * nb * rp), 256, 0, w.s>>>(wA[wi].as<double2>(), Z, rt, nb, rp, 1);
+        TFMM_CUDA_CHECK(cudaGetLastError());
+        double2* G3 = d_G3.as<double2>() + g3_off[t];
+        if (nb <= m)
+            CUBLAS_CHECK(cublasZherk(w.blas, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, nb, m, &r_one,
+                                     (const cuDoubleComplex*)Z, nb, &r_zero, (cuDoubleComplex*)G3, nb));
+        else
+            CUBLAS_CHECK(cublasZherk(w.blas, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_C, m, nb, &r_one,
+                                     (const cuDoubleComplex*)Z, nb, &r_zero, (cuDoubleComplex*)G3, m));
+        auto tb = std::chrono::steady_clock::now();
+        ms_g[wi] += std::chrono::duration<double, std::milli>(tb - ta).count();
+        double* Wt = d_W3.as<double>() + (int64_t)t * n3max;
+        const double thr2 = tol2 * T[t].norm2;
+        int meig = n;
+        if (use_dx && thr2 > 0.0) {
+            double vl = 0.5 * thr2 / n, vu = 2.0 * T[t].z2 + 1.0;
+            int64_t meig64 = 0;
+            CUSOLVER_CHECK(cusolverDnXsyevdx(w.sol, w.prm, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_V,
+                                             CUBLAS_FILL_MODE_LOWER, n, CUDA_C_64F, G3, n, &vl, &vu, 0, 0, &meig64,
+                                             CUDA_R_64F, Wt, CUDA_C_64F, weig[wi].p, eig_d, weigh[wi].data(), eig_h,
+                                             winfo[wi].as<int>()));
+            meig = (int)meig64;
+        } else {
+            CUSOLVER_CHECK(cusolverDnXsyevd(w.sol, w.prm, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n,
+                                            CUDA_C_64F, G3, n, CUDA_R_64F, Wt, CUDA_C_64F, weig[wi].p, eig_d,
+                                            weigh[wi].data(), eig_h, winfo[wi].as<int>()));
+        }
+        int hinfo = 0;
+        W3[t].resize(std::max(meig, 0));
+        if (meig > 0)
+            TFMM_CUDA_CHECK(cudaMemcpyAsync(W3[t].data(), Wt, sizeof(double) * meig, cudaMemcpyDeviceToHost, w.s));
+        TFMM_CUDA_CHECK(cudaMemcpyAsync(&hinfo, winfo[wi].p, sizeof(int), cudaMemcpyDeviceToHost, w.s));
+        TFMM_CUDA_CHECK(cudaStreamSynchronize(w.s));
+        if (hinfo != 0) fail(TFMM_NUMERIC, "eigen-decomposition failed (info " + std::to_string(hinfo) + ")");
+        if (meig < 1) fail(TFMM_NUMERIC, "no eigenvalue above the truncation bound (zero far-field tensor?)");
+        // energy left out of the returned eigenvalues (all of it below the bound vl)
+        double ret = 0.0;
+        for (double v : W3[t]) ret += std::max(v, 0.0);
+        const double unret = meig < n ? std::max(T[t].z2 - ret, 0.0) : 0.0;
+        T[t].rb = choose_rank(W3[t].data(), meig, thr2, unret);
+        nvec[t] = meig;
+        ms_e[wi] += ms_since(tb);
+    });
+    // one allocation for the batch's FP64 factors
+    int64_t f_tot = 0;
+    std::vector<int64_t> f_off(nT);
+    int rbmax = 1;
+    for (int t = 0; t < nT; ++t) {
+        const int rt = T[t].rt, rp = T[t].rp, rb = T[t].rb, nb = T[t].nb;
+        f_off[t] = f_tot;
+        f_tot += (int64_t)nt * rt + (int64_t)np * rp + (int64_t)nb * rb + (int64_t)rt * rp * rb;
+        rbmax = std::max(rbmax, rb);
+    }
+    double2* arena = nullptr;
+    TFMM_CUDA_CHECK(cudaMalloc(&arena, sizeof(double2) * std::max<int64_t>(f_tot, 1)));
+    P.f64_arenas.push_back(arena);
+    // QR workspace per worker
+    int qr_lw = 1;
+    {
+        Worker& w0 = *pool[0];
+        for (int t = 0; t < nT; ++t) {
+            const int m = T[t].rt * T[t].rp, nb = T[t].nb, rb = T[t].rb;
+            if (nb <= m) continue;
+            int l1 = 0, l2 = 0;
+            CUSOLVER_CHECK(cusolverDnZgeqrf_bufferSize(w0.sol, nb, rb, (cuDoubleComplex*)arena, nb, &l1));
+            CUSOLVER_CHECK(cusolverDnZungqr_bufferSize(w0.sol, nb, rb, rb, (cuDoubleComplex*)arena, nb,
+                                                       (const cuDoubleComplex*)arena, &l2));
+            qr_lw = std::max(qr_lw, std::max(l1, l2));
+        }
+    }
+    std::vector<DevBuf> wqr(nw), wtau(nw), wC3(nw);
+    for (int i = 0; i < nw; ++i) {
+        wqr[i].alloc(sizeof(double2) * qr_lw);
+        wtau[i].alloc(sizeof(double2) * rbmax);
+        wC3[i].alloc(sizeof(double2) * (int64_t)mmax * rbmax);
+    }
+    parallel_for(pool, nT, [&](Worker& w, int wi, int t) {
+        auto tc = std::chrono::steady_clock::now();
+        const int rt = T[t].rt, rp = T[t].rp, nb = T[t].nb, m = rt * rp, rb = T[t].rb;
+        HostFactors64& F = P.f64[(size_t)T[t].g * 2 + T[t].alpha];
+        F.rt = rt; F.rp = rp; F.rb = rb;
+        F.base = arena + f_off[t];
+        const int64_t e_ut = (int64_t)nt * rt, e_up = (int64_t)np * rp, e_ub = (int64_t)nb * rb;
+        double2* Ut = F.base;
+        double2* Up = Ut + e_ut;
+        double2* Ub = Up + e_up;
+        double2* Cc = Ub + e_ub;
+        const double2* Z = d_Z.as<double2>() + z_off[t];
+        const double2* G3 = d_G3.as<double2>() + g3_off[t];
+        double2* Vp = wV[wi].as<double2>();
+        TFMM_CUDA_CHECK(cudaMemcpyAsync(Ut, d_Ut.as<double2>() + (int64_t)t * nt * nt, sizeof(double2) * e_ut,
+                                        cudaMemcpyDeviceToDevice, w.s));
+        // U_phi = conj(V_r)
+        take_top_kernel<<<grid1d((int64_t)np * rp), 256, 0, w.s>>>(d_G2.as<double2>() + (int64_t)t * np * np, np, np,
+                                                                     np - 1, rp, Up, 1);
+        if (nb <= m) {
+            // U_beta = leading eigenvectors of Z Z^H
+            take_top_kernel<<<grid1d(e_ub), 256, 0, w.s>>>(G3, nb, nb, nvec[t] - 1, rb, Ub, 0);
+        } else {
+            // Q0 = Z V_r (V_r: leading eigenvectors of Z^H Z), U_beta = orthonormal basis of Q0
+            take_top_kernel<<<grid1d((int64_t)m * rb), 256, 0, w.s>>>(G3, m, m, nvec[t] - 1, rb, Vp, 0);
+            CUBLAS_CHECK(cublasZgemm(w.blas, CUBLAS_OP_N, CUBLAS_OP_N, nb, rb, m, &one, (const cuDoubleComplex*)Z, nb,
+                                     (const cuDoubleComplex*)Vp, m, &zero, (cuDoubleComplex*)Ub, nb));
+            CUSOLVER_CHECK(cusolverDnZgeqrf(w.sol, nb, rb, (cuDoubleComplex*)Ub, nb, (cuDoubleComplex*)wtau[wi].p,
+                                            (cuDoubleComplex*)wqr[wi].p, qr_lw, winfo[wi].as<int>()));
+            CUSOLVER_CHECK(cusolverDnZungqr(w.sol, nb, rb, rb, (cuDoubleComplex*)Ub, nb,
+                                            (const cuDoubleComplex*)wtau[wi].p, (cuDoubleComplex*)wqr[wi].p, qr_lw,
+                                            winfo[wi].as<int>()));
+            int hinfo = 0;
+            TFMM_CUDA_CHECK(cudaMemcpyAsync(&hinfo, winfo[wi].p, sizeof(int), cudaMemcpyDeviceToHost, w.s));
+            TFMM_CUDA_CHECK(cudaStreamSynchronize(w.s));
+            if (hinfo != 0) fail(TFMM_NUMERIC, "QR of the beta factor failed");
+        }
+        // core: C_(3) = U_beta^H Z (r_b x m), stored as the r_t x r_p x r_b tensor (m x r_b)
+        CUBLAS_CHECK(cublasZgemm(w.blas, CUBLAS_OP_C, CUBLAS_OP_N, rb, m, nb, &one, (const cuDoubleComplex*)Ub, nb,
+                                 (const cuDoubleComplex*)Z, nb, &zero, (cuDoubleComplex*)wC3[wi].p, rb));
+        CUBLAS_CHECK(cublasZgeam(w.blas, CUBLAS_OP_T, CUBLAS_OP_T, m, rb, &one, (const cuDoubleComplex*)wC3[wi].p, rb,
+                                 &zero, (const cuDoubleComplex*)wC3[wi].p, rb, (cuDoubleComplex*)Cc, m));
+        TFMM_CUDA_CHECK(cudaGetLastError());
+        TFMM_CUDA_CHECK(cudaStreamSynchronize(w.s));  // wC3 / wV are reused by this worker's next tensor
+        ms_f[wi] += ms_since(tc);
+        int* rk = &P.ranks[((size_t)T[t].g * 2 + T[t].alpha) * 3];
+        rk[0] = rt; rk[1] = rp; rk[2] = rb;
+    });
+    const double wall = ms_since(t0);
+    double sg = 0, se = 0, sf = 0;
+    for (int i = 0; i < nw; ++i) { sg += ms_g[i]; se += ms_e[i]; sf += ms_f[i]; }
+    const double tot = std::max(sg + se + sf, 1e-9);
+    tm.gram3 += wall * sg / tot;
+    tm.eig3 += wall * se / tot;
+    tm.fac3 += wall * sf / tot;
+}
 
 }  // namespace
 
@@ -421,18 +988,11 @@ void build_tucker_setup(Plan& P, const Mesh& M, cudaStream_t s) {
         TFMM_CUDA_CHECK(cudaMalloc(&P.d_dense, sizeof(float2) * std::max<int64_t>(P.dense_elems, 1)));
     }
 
-    cublasHandle_t blas;
-    cusolverDnHandle_t sol;
-    cusolverDnParams_t sprm;
-    CUBLAS_CHECK(cublasCreate(&blas));
-    CUBLAS_CHECK(cublasSetStream(blas, s));
-    CUSOLVER_CHECK(cusolverDnCreate(&sol));
-    CUSOLVER_CHECK(cusolverDnSetStream(sol, s));
-    CUSOLVER_CHECK(cusolverDnCreateParams(&sprm));
-    struct Guard {
-        cublasHandle_t b; cusolverDnHandle_t s; cusolverDnParams_t p;
-        ~Guard() { cusolverDnDestroyParams(p); cusolverDnDestroy(s); cublasDestroy(b); }
-    } guard{blas, sol, sprm};
+    int nworkers = 8;
+    if (const char* e = std::getenv("TFMM_SETUP_STREAMS")) nworkers = std::max(1, std::min(64, std::atoi(e)));
+    std::vector<std::unique_ptr<Worker>> pool;
+    for (int i = 0; i < nworkers; ++i) pool.emplace_back(new Worker());
+    Timers timers;
 
     // batches of groups bounded by a device-memory budget
     size_t free_b = 0, total_b = 0;
@@ -446,8 +1006,6 @@ void build_tucker_setup(Plan& P, const Mesh& M, cudaStream_t s) {
     P.ranks.assign((size_t)P.G * 6, 0);
     double ms_ff = 0, ms_svd = 0;
 
-    const double r_one = 1.0, r_zero = 0.0;  // herk scalars
-    const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0), zero = make_cuDoubleComplex(0.0, 0.0);
     int g0 = 0;
     while (g0 < P.G) {
         int g1 = g0;
@@ -516,202 +1074,7 @@ void build_tucker_setup(Plan& P, const Mesh& M, cudaStream_t s) {
         for (int b = 0; b < nbg; ++b)
             for (int al = 0; al < 2; ++al)
                 T.push_back(Tensor{g0 + b, al, nbeta[b], d_A.as<double2>() + out_off[b] + (int64_t)al * nd * nbeta[b]});
-        const int nT = (int)T.size();
-        const double tol2 = prm.tol * prm.tol / 3.0;
-
-        // mode theta: G1 = A_(1) A_(1)^H
-        DevBuf d_G1(sizeof(double2) * nT * nt * nt), d_W1(sizeof(double) * nT * nt);
-        for (int t = 0; t < nT; ++t)
-            CUBLAS_CHECK(cublasZherk(blas, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, nt, np * T[t].nb, &r_one,
-                                     (const cuDoubleComplex*)T[t].A, nt, &r_zero,
-                                     (cuDoubleComplex*)(d_G1.as<double2>() + (int64_t)t * nt * nt), nt));
-        eig_batched(sol, sprm, d_G1.as<double2>(), d_W1.as<double>(), nt, nT, s);
-        std::vector<double> W1((size_t)nT * nt);
-        TFMM_CUDA_CHECK(cudaMemcpyAsync(W1.data(), d_W1.p, sizeof(double) * W1.size(), cudaMemcpyDeviceToHost, s));
-        TFMM_CUDA_CHECK(cudaStreamSynchronize(s));
-        int64_t y1_tot = 0;
-        std::vector<int64_t> y1_off(nT);
-        for (int t = 0; t < nT; ++t) {
-            double n2 = 0;
-            for (int i = 0; i < nt; ++i) n2 += std::max(W1[(size_t)t * nt + i], 0.0);
-            T[t].norm2 = n2;
-            T[t].rt = choose_rank(&W1[(size_t)t * nt], nt, tol2 * n2);
-            y1_off[t] = y1_tot;
-            y1_tot += (int64_t)T[t].rt * np * T[t].nb;
-        }
-        // U_theta (n_theta x r_t), A1 = U_theta^H A_(1) -> [a, i_phi, n], Y1 = [a, n, i_phi]
-        DevBuf d_Ut(sizeof(double2) * nT * nt * nt);
-        DevBuf d_A1(sizeof(double2) * std::max<int64_t>(y1_tot, 1)), d_Y1(sizeof(double2) * std::max<int64_t>(y1_tot, 1));
-        for (int t = 0; t < nT; ++t) {
-            double2* Ut = d_Ut.as<double2>() + (int64_t)t * nt * nt;
-            take_top_kernel<<<grid1d((int64_t)nt * T[t].rt), 256, 0, s>>>(d_G1.as<double2>() + (int64_t)t * nt * nt, nt,
-                                                                           nt, nt - 1, T[t].rt, Ut, 0);
-            CUBLAS_CHECK(cublasZgemm(blas, CUBLAS_OP_C, CUBLAS_OP_N, T[t].rt, np * T[t].nb, nt, &one,
-                                     (const cuDoubleComplex*)Ut, nt, (const cuDoubleComplex*)T[t].A, nt, &zero,
-                                     (cuDoubleComplex*)(d_A1.as<double2>() + y1_off[t]), T[t].rt));
-            permute3_kernel<<<grid1d((int64_t)T[t].rt * np * T[t].nb), 256, 0, s>>>(d_A1.as<double2>() + y1_off[t],
-                                                          d_Y1.as<double2>() + y1_off[t], T[t].rt, np, T[t].nb, 0);
-        }
-        TFMM_CUDA_CHECK(cudaGetLastError());
-        d_A1.release();
-        // mode phi: G2' = Y1^H Y1 (= conj of the mode-2 Gram)
-        DevBuf d_G2(sizeof(double2) * nT * np * np), d_W2(sizeof(double) * nT * np);
-        for (int t = 0; t < nT; ++t)
-            CUBLAS_CHECK(cublasZherk(blas, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_C, np, T[t].rt * T[t].nb, &r_one,
-                                     (const cuDoubleComplex*)(d_Y1.as<double2>() + y1_off[t]), T[t].rt * T[t].nb,
-                                     &r_zero, (cuDoubleComplex*)(d_G2.as<double2>() + (int64_t)t * np * np), np));
-        eig_batched(sol, sprm, d_G2.as<double2>(), d_W2.as<double>(), np, nT, s);
-        std::vector<double> W2((size_t)nT * np);
-        TFMM_CUDA_CHECK(cudaMemcpyAsync(W2.data(), d_W2.p, sizeof(double) * W2.size(), cudaMemcpyDeviceToHost, s));
-        TFMM_CUDA_CHECK(cudaStreamSynchronize(s));
-        int64_t z_tot = 0;
-        std::vector<int64_t> z_off(nT);
-        for (int t = 0; t < nT; ++t) {
-            T[t].rp = choose_rank(&W2[(size_t)t * np], np, tol2 * T[t].norm2);
-            z_off[t] = z_tot;
-            z_tot += (int64_t)T[t].rt * T[t].rp * T[t].nb;
-        }
-        // V_r (n_phi x r_p); A2 = Y1 V_r -> [a, n, b]; Z = [n, a, b]; U_phi = conj(V_r)
-        DevBuf d_Vp(sizeof(double2) * nT * np * np), d_Up(sizeof(double2) * nT * np * np);
-        DevBuf d_A2(sizeof(double2) * std::max<int64_t>(z_tot, 1)), d_Z(sizeof(double2) * std::max<int64_t>(z_tot, 1));
-        for (int t = 0; t < nT; ++t) {
-            const int rt = T[t].rt, rp = T[t].rp, nb = T[t].nb;
-            double2* Vp = d_Vp.as<double2>() + (int64_t)t * np * np;
-            take_top_kernel<<<grid1d((int64_t)np * rp), 256, 0, s>>>(d_G2.as<double2>() + (int64_t)t * np * np, np, np,
-                                                                      np - 1, rp, Vp, 0);
-            take_top_kernel<<<grid1d((int64_t)np * rp), 256, 0, s>>>(d_G2.as<double2>() + (int64_t)t * np * np, np, np,
-                                                                      np - 1, rp, d_Up.as<double2>() + (int64_t)t * np * np, 1);
-            CUBLAS_CHECK(cublasZgemm(blas, CUBLAS_OP_N, CUBLAS_OP_N, rt * nb, rp, np, &one,
-                                     (const cuDoubleComplex*)(d_Y1.as<double2>() + y1_off[t]), rt * nb,
-                                     (const cuDoubleComplex*)Vp, np, &zero,
-                                     (cuDoubleComplex*)(d_A2.as<double2>() + z_off[t]), rt * nb));
-            permute3_kernel<<<grid1d((int64_t)rt * nb * rp), 256, 0, s>>>(d_A2.as<double2>() + z_off[t], d_Z.as<double2>() + z_off[t],
-                                                         rt, nb, rp, 1);
-        }
-        TFMM_CUDA_CHECK(cudaGetLastError());
-        d_Y1.release();
-        d_A2.release();
-        // mode beta: Gram of the smaller side of Z (n_beta x m, m = r_t r_p)
-        std::vector<int> n3(nT), bucket(nT);
-        for (int t = 0; t < nT; ++t) {
-            const int m = T[t].rt * T[t].rp;
-            n3[t] = std::min(T[t].nb, m);
-            bucket[t] = (int)round_up(n3[t], 32);
-        }
-        std::vector<int> bsizes(bucket);
-        std::sort(bsizes.begin(), bsizes.end());
-        bsizes.erase(std::unique(bsizes.begin(), bsizes.end()), bsizes.end());
-        std::vector<std::vector<double>> W3(nT);
-        std::vector<int64_t> gram_off(nT);
-        std::vector<int> gram_ld(nT);
-        DevBuf d_G3all;
-        {
-            int64_t g3_tot = 0;
-            for (int t = 0; t < nT; ++t) {
-                gram_off[t] = g3_tot;
-                gram_ld[t] = bucket[t];
-                g3_tot += (int64_t)bucket[t] * bucket[t];
-            }
-            d_G3all.alloc(sizeof(double2) * g3_tot);
-        }
-        DevBuf d_tmp;
-        for (int bs : bsizes) {
-            std::vector<int> members;
-            for (int t = 0; t < nT; ++t)
-                if (bucket[t] == bs) members.push_back(t);
-            // contiguous batch buffer for this bucket
-            DevBuf d_Gb(sizeof(double2) * (int64_t)members.size() * bs * bs), d_Wb(sizeof(double) * members.size() * bs);
-            for (size_t q = 0; q < members.size(); ++q) {
-                const int t = members[q];
-                const int rt = T[t].rt, rp = T[t].rp, nb = T[t].nb, m = rt * rp, n = n3[t];
-                double2* Gq = d_Gb.as<double2>() + (int64_t)q * bs * bs;
-                const double2* Z = d_Z.as<double2>() + z_off[t];
-                d_tmp.alloc(sizeof(double2) * (int64_t)n * n);
-                if (nb <= m)
-                    CUBLAS_CHECK(cublasZherk(blas, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, nb, m, &r_one,
-                                             (const cuDoubleComplex*)Z, nb, &r_zero, (cuDoubleComplex*)d_tmp.p, nb));
-                else
-                    CUBLAS_CHECK(cublasZherk(blas, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_C, m, nb, &r_one,
-                                             (const cuDoubleComplex*)Z, nb, &r_zero, (cuDoubleComplex*)d_tmp.p, m));
-                copy_lower_kernel<<<grid1d((int64_t)n * n), 256, 0, s>>>(d_tmp.as<double2>(), n, Gq, bs);
-                pad_gram_kernel<<<grid1d((int64_t)bs * bs), 256, 0, s>>>(Gq, n, bs, -(T[t].norm2 + 1.0));
-                TFMM_CUDA_CHECK(cudaStreamSynchronize(s));  // d_tmp is reused
-            }
-            TFMM_CUDA_CHECK(cudaGetLastError());
-            eig_batched(sol, sprm, d_Gb.as<double2>(), d_Wb.as<double>(), bs, (int)members.size(), s);
-            std::vector<double> Wb(members.size() * (size_t)bs);
-            TFMM_CUDA_CHECK(cudaMemcpyAsync(Wb.data(), d_Wb.p, sizeof(double) * Wb.size(), cudaMemcpyDeviceToHost, s));
-            for (size_t q = 0; q < members.size(); ++q)
-                TFMM_CUDA_CHECK(cudaMemcpyAsync(d_G3all.as<double2>() + gram_off[members[q]],
-                                                d_Gb.as<double2>() + (int64_t)q * bs * bs,
-                                                sizeof(double2) * (int64_t)bs * bs, cudaMemcpyDeviceToDevice, s));
-            TFMM_CUDA_CHECK(cudaStreamSynchronize(s));
-            for (size_t q = 0; q < members.size(); ++q) {
-                const int t = members[q];
-                // padded eigenvalues come first (they are negative); the true ones are the last n3
-                W3[t].assign(Wb.begin() + q * bs + (bs - n3[t]), Wb.begin() + (q + 1) * bs);
-            }
-        }
-        d_tmp.release();
-        // factors and cores
-        for (int t = 0; t < nT; ++t) {
-            const int rt = T[t].rt, rp = T[t].rp, nb = T[t].nb, m = rt * rp, n = n3[t], bs = gram_ld[t];
-            T[t].rb = choose_rank(W3[t].data(), n, tol2 * T[t].norm2);
-            const int rb = T[t].rb;
-            HostFactors64& F = P.f64[(size_t)T[t].g * 2 + T[t].alpha];
-            F.rt = rt; F.rp = rp; F.rb = rb;
-            const int64_t e_ut = (int64_t)nt * rt, e_up = (int64_t)np * rp, e_ub = (int64_t)nb * rb,
-                          e_c = (int64_t)m * rb;
-            TFMM_CUDA_CHECK(cudaMalloc(&F.base, sizeof(double2) * (e_ut + e_up + e_ub + e_c)));
-            double2* Ut = F.base;
-            double2* Up = Ut + e_ut;
-            double2* Ub = Up + e_up;
-            double2* Cc = Ub + e_ub;
-            TFMM_CUDA_CHECK(cudaMemcpyAsync(Ut, d_Ut.as<double2>() + (int64_t)t * nt * nt, sizeof(double2) * e_ut,
-                                            cudaMemcpyDeviceToDevice, s));
-            TFMM_CUDA_CHECK(cudaMemcpyAsync(Up, d_Up.as<double2>() + (int64_t)t * np * np, sizeof(double2) * e_up,
-                                            cudaMemcpyDeviceToDevice, s));
-            const double2* Z = d_Z.as<double2>() + z_off[t];
-            const double2* G3 = d_G3all.as<double2>() + gram_off[t];
-            if (nb <= m) {
-                // U_beta = leading eigenvectors of Z Z^H: rows 0..nb-1 of the last columns of the
-                // padded problem (its padding eigenvalues are negative and come first)
-                take_top_kernel<<<grid1d(e_ub), 256, 0, s>>>(G3, bs, nb, bs - 1, rb, Ub, 0);
-            } else {
-                // Q0 = Z V_r, then U_beta = orthonormal basis of Q0 (Householder QR)
-                DevBuf d_V(sizeof(double2) * (int64_t)m * rb), d_Q(sizeof(double2) * e_ub);
-                take_top_kernel<<<grid1d((int64_t)m * rb), 256, 0, s>>>(G3, bs, m, bs - 1, rb, d_V.as<double2>(), 0);
-                CUBLAS_CHECK(cublasZgemm(blas, CUBLAS_OP_N, CUBLAS_OP_N, nb, rb, m, &one,
-                                         (const cuDoubleComplex*)Z, nb, (const cuDoubleComplex*)d_V.p, m, &zero,
-                                         (cuDoubleComplex*)Ub, nb));
-                int lwork = 0, lwork2 = 0;
-                CUSOLVER_CHECK(cusolverDnZgeqrf_bufferSize(sol, nb, rb, (cuDoubleComplex*)Ub, nb, &lwork));
-                DevBuf d_tau(sizeof(double2) * rb), d_info(sizeof(int));
-                CUSOLVER_CHECK(cusolverDnZungqr_bufferSize(sol, nb, rb, rb, (cuDoubleComplex*)Ub, nb,
-                                                           (const cuDoubleComplex*)d_tau.p, &lwork2));
-                DevBuf d_work(sizeof(double2) * std::max(std::max(lwork, lwork2), 1));
-                CUSOLVER_CHECK(cusolverDnZgeqrf(sol, nb, rb, (cuDoubleComplex*)Ub, nb, (cuDoubleComplex*)d_tau.p,
-                                                (cuDoubleComplex*)d_work.p, std::max(lwork, lwork2), d_info.as<int>()));
-                CUSOLVER_CHECK(cusolverDnZungqr(sol, nb, rb, rb, (cuDoubleComplex*)Ub, nb,
-                                                (const cuDoubleComplex*)d_tau.p, (cuDoubleComplex*)d_work.p,
-                                                std::max(lwork, lwork2), d_info.as<int>()));
-                int hinfo = 0;
-                TFMM_CUDA_CHECK(cudaMemcpyAsync(&hinfo, d_info.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-                TFMM_CUDA_CHECK(cudaStreamSynchronize(s));
-                if (hinfo != 0) fail(TFMM_NUMERIC, "QR of the beta factor failed");
-            }
-            // core: C_(3) = U_beta^H Z (r_b x m), stored as the r_t x r_p x r_b tensor (m x r_b)
-            DevBuf d_C3(sizeof(double2) * e_c);
-            CUBLAS_CHECK(cublasZgemm(blas, CUBLAS_OP_C, CUBLAS_OP_N, rb, m, nb, &one, (const cuDoubleComplex*)Ub, nb,
-                                     (const cuDoubleComplex*)Z, nb, &zero, (cuDoubleComplex*)d_C3.p, rb));
-            CUBLAS_CHECK(cublasZgeam(blas, CUBLAS_OP_T, CUBLAS_OP_T, m, rb, &one, (const cuDoubleComplex*)d_C3.p, rb,
-                                     &zero, (const cuDoubleComplex*)d_C3.p, rb, (cuDoubleComplex*)Cc, m));
-            TFMM_CUDA_CHECK(cudaStreamSynchronize(s));  // temporaries of this tensor are released here
-            int* rk = &P.ranks[((size_t)T[t].g * 2 + T[t].alpha) * 3];
-            rk[0] = rt; rk[1] = rp; rk[2] = rb;
-        }
-        TFMM_CUDA_CHECK(cudaGetLastError());
-        TFMM_CUDA_CHECK(cudaStreamSynchronize(s));
+        hosvd_batch(P, T, pool, s, timers);
         ms_svd += ms_since(t0);
         g0 = g1;
     }
@@ -722,6 +1085,12 @@ void build_tucker_setup(Plan& P, const Mesh& M, cudaStream_t s) {
     P.setup_ms[1] = ms_svd;
     P.setup_ms[2] = ms_since(t0);
     P.setup_ms[3] = ms_since(t_all);
+    if (std::getenv("TFMM_VERBOSE"))
+        std::fprintf(stderr,
+                     "[tfmm setup] far-field %.1f ms, HOSVD %.1f ms (mode1 %.1f, mode2 %.1f, mode3 gram %.1f, "
+                     "mode3 eig %.1f, mode3 factors %.1f), pack %.1f ms, %d workers\n",
+                     ms_ff, ms_svd, timers.mode1, timers.mode2, timers.gram3, timers.eig3, timers.fac3,
+                     P.setup_ms[2], (int)pool.size());
 }
 
 void farfield_group_host(const Plan& P, int g, double2* At, double2* Ap, cudaStream_t s) {

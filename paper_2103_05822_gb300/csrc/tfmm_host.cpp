@@ -347,13 +347,22 @@ tfmm_status tfmm_plan_from_tucker(int64_t n_rwg, int32_t n_groups, int32_t n_the
                 const int* rk = &P.ranks[((size_t)g * 2 + al) * 3];
                 TFMM_REQUIRE(rk[0] >= 1 && rk[0] <= n_theta && rk[1] >= 1 && rk[1] <= n_phi && rk[2] >= 1 && rk[2] <= nb,
                              "rank out of range for group " + std::to_string(g));
-                const int64_t e = (int64_t)n_theta * rk[0] + (int64_t)n_phi * rk[1] + nb * rk[2] +
-                                  (int64_t)rk[0] * rk[1] * rk[2];
+                pos += (int64_t)n_theta * rk[0] + (int64_t)n_phi * rk[1] + nb * rk[2] + (int64_t)rk[0] * rk[1] * rk[2];
+            }
+        }
+        double2* arena = nullptr;
+        TFMM_CUDA_CHECK(cudaMalloc(&arena, sizeof(double2) * pos));
+        P.f64_arenas.push_back(arena);
+        TFMM_CUDA_CHECK(cudaMemcpyAsync(arena, src, sizeof(double2) * pos, cudaMemcpyHostToDevice, s));
+        pos = 0;
+        for (int g = 0; g < n_groups; ++g) {
+            const int64_t nb = P.grp_off[g + 1] - P.grp_off[g];
+            for (int al = 0; al < 2; ++al) {
+                const int* rk = &P.ranks[((size_t)g * 2 + al) * 3];
                 HostFactors64& F = P.f64[(size_t)g * 2 + al];
                 F.rt = rk[0]; F.rp = rk[1]; F.rb = rk[2];
-                TFMM_CUDA_CHECK(cudaMalloc(&F.base, sizeof(double2) * e));
-                TFMM_CUDA_CHECK(cudaMemcpyAsync(F.base, src + pos, sizeof(double2) * e, cudaMemcpyHostToDevice, s));
-                pos += e;
+                F.base = arena + pos;
+                pos += (int64_t)n_theta * rk[0] + (int64_t)n_phi * rk[1] + nb * rk[2] + (int64_t)rk[0] * rk[1] * rk[2];
             }
         }
         pack_factors_fp32(P, s);
