@@ -219,6 +219,27 @@ tfmm_status tfmm_matvec_host(tfmm_plan* plan, const tfmm_cfloat* x_host, tfmm_cf
 tfmm_status tfmm_planewave(const tfmm_plan* plan, const double* khat, const double* pol, int32_t R,
                            tfmm_cfloat* V, void* stream);
 
+/* Allocation-free variant of tfmm_planewave.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory while they
+ * call the library, such as applications whose device memory is all handed out
+ * by their own pool allocator (a cudaMalloc from the library would fail or
+ * fragment that pool) or loops that cannot afford the device-wide
+ * synchronisation a cudaFree implies.  Instead of a per-call allocation, the
+ * incidence table is staged in one fixed array inside the library: at most
+ * 1024 incidences (48 KiB), present on every GPU that loads the library until
+ * the process exits.  The call allocates and frees nothing and returns without
+ * synchronising the stream.
+ *   khat, pol  host, R x 3, as tfmm_planewave (copied before the call returns)
+ *   V          device, n_rwg x R FP32 complex, overwritten
+ *   R          1..1024; a larger R returns INVALID_ARG with a message
+ * The first call on a device looks up the device address of the table (once
+ * per device, with that device current).  Every call shares the one table and
+ * overwrites the entries it uses; calls that overlap on the GPU (different
+ * streams or threads) race on it, so order them on one stream.
+ * Errors: INVALID_ARG, CUDA.  Needs a plan made by tfmm_plan_create. */
+tfmm_status tfmm_planewave_noalloc(const tfmm_plan* plan, const double* khat, const double* pol, int32_t R,
+                                   tfmm_cfloat* V, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

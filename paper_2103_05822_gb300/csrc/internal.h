@@ -140,6 +140,7 @@ struct Plan {
 void build_tucker_setup(Plan& P, const Mesh& M, cudaStream_t s);
 void farfield_group_host(const Plan& P, int g, double2* At, double2* Ap, cudaStream_t s);
 void planewave_rhs(const Plan& P, const double* khat, const double* pol, int R, float2* V, cudaStream_t s);
+void planewave_rhs_noalloc(const Plan& P, const double* khat, const double* pol, int R, float2* V, cudaStream_t s);
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
 
 // apply.cu

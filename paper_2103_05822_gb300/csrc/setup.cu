@@ -26,6 +26,7 @@
 #include <cstdio>
 #include <exception>
 #include <memory>
+#include <mutex>
 #include <thread>
 
 #include "internal.h"
@@ -1148,6 +1149,63 @@ void planewave_rhs(const Plan& P, const double* khat, const double* pol, int R, 
     planewave_kernel<<<grid, 256, 0, s>>>(a);
     TFMM_CUDA_CHECK(cudaGetLastError());
     TFMM_CUDA_CHECK(cudaStreamSynchronize(s));
+}
+
+// ------------------------------------------------ allocation-free excitation
+// Some callers cannot allocate device memory while they call into the library:
+// applications whose device memory is all handed out by their own pool
+// allocator (a library cudaMalloc would fail or fragment that pool), and loops
+// that cannot afford the device-wide synchronisation a cudaFree implies.  For
+// them tfmm_planewave_noalloc stages the incidence table in this fixed array
+// instead of a per-call allocation.  It holds kNoAllocMaxIncidences directions
+// and polarisations (6 doubles each, 48 KiB); every GPU that loads the library
+// keeps it until the process exits.  All calls share it.
+constexpr int kNoAllocMaxIncidences = 1024;
+static __device__ __align__(256) double g_pw_table[6 * kNoAllocMaxIncidences];
+
+namespace {
+std::mutex g_pw_table_mu;
+double* g_pw_table_addr[256] = {};
+
+// Device address of g_pw_table on the current device, looked up once per device
+// (a host-side reference to g_pw_table is only a stand-in, not that address).
+double* pw_table_address() {
+    int dev = 0;
+    TFMM_CUDA_CHECK(cudaGetDevice(&dev));
+    TFMM_REQUIRE(dev >= 0 && dev < 256, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_pw_table_mu);
+    if (!g_pw_table_addr[dev]) {
+        void* p = nullptr;
+        TFMM_CUDA_CHECK(cudaGetSymbolAddress(&p, g_pw_table));
+        g_pw_table_addr[dev] = static_cast<double*>(p);
+    }
+    return g_pw_table_addr[dev];
+}
+}  // namespace
+
+void planewave_rhs_noalloc(const Plan& P, const double* khat, const double* pol, int R, float2* V, cudaStream_t s) {
+    TFMM_REQUIRE(P.has_geometry && P.d_geom, "plan has no geometry (built from factors)");
+    TFMM_REQUIRE(R >= 1 && R <= kNoAllocMaxIncidences,
+                 "R = " + std::to_string(R) + " incidences exceed the static table of " +
+                     std::to_string(kNoAllocMaxIncidences) + "; split the sweep or call tfmm_planewave");
+    double* table = pw_table_address();
+    upload_quadrature(P.params.quad_order, s);
+    // every entry the kernel reads is overwritten here: nothing has to start at zero
+    TFMM_CUDA_CHECK(cudaMemcpyAsync(table, khat, sizeof(double) * 3 * R, cudaMemcpyHostToDevice, s));
+    TFMM_CUDA_CHECK(cudaMemcpyAsync(table + 3 * kNoAllocMaxIncidences, pol, sizeof(double) * 3 * R,
+                                    cudaMemcpyHostToDevice, s));
+    PWArgs a;
+    a.geom = P.d_geom;
+    a.khat = table;
+    a.pol = table + 3 * kNoAllocMaxIncidences;
+    a.V = V;
+    a.k = P.k;
+    a.n = P.N;
+    a.R = R;
+    a.nq = P.params.quad_order * P.params.quad_order;
+    dim3 grid((unsigned)((P.N + 255) / 256), R);
+    planewave_kernel<<<grid, 256, 0, s>>>(a);
+    TFMM_CUDA_CHECK(cudaGetLastError());
 }
 
 }  // namespace tfmm

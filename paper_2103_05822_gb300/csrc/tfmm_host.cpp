@@ -576,4 +576,12 @@ tfmm_status tfmm_planewave(const tfmm_plan* plan, const double* khat, const doub
     });
 }
 
+tfmm_status tfmm_planewave_noalloc(const tfmm_plan* plan, const double* khat, const double* pol, int32_t R,
+                                   tfmm_cfloat* V, void* stream) {
+    return guarded([&] {
+        TFMM_REQUIRE(plan && khat && pol && V, "null argument");
+        planewave_rhs_noalloc(plan->p, khat, pol, R, reinterpret_cast<float2*>(V), (cudaStream_t)stream);
+    });
+}
+
 }  // extern "C"

@@ -25,7 +25,7 @@ EXPORTED = [
     "tfmm_plan_group", "tfmm_plan_members", "tfmm_plan_centres", "tfmm_plan_quadrature",
     "tfmm_plan_export_factors", "tfmm_plan_farfield", "tfmm_plan_destroy",
     "tfmm_aggregate", "tfmm_disaggregate", "tfmm_aggregate_dense", "tfmm_disaggregate_dense",
-    "tfmm_matvec_host", "tfmm_planewave",
+    "tfmm_matvec_host", "tfmm_planewave", "tfmm_planewave_noalloc",
 ]
 
 
@@ -103,6 +103,7 @@ def load():
         "tfmm_disaggregate_dense": [P, P, I32, I32, cfloat, P, I64, P],
         "tfmm_matvec_host": [P, P, P, I32, I32, P],
         "tfmm_planewave": [P, P, P, I32, P, P],
+        "tfmm_planewave_noalloc": [P, P, P, I32, P, P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -349,3 +350,11 @@ def tfmm_planewave(plan, khat, pol, V, stream=None):
     k = np.ascontiguousarray(khat, np.float64).reshape(-1, 3)
     p = np.ascontiguousarray(pol, np.float64).reshape(-1, 3)
     _check(load().tfmm_planewave(plan.handle, _np_ptr(k), _np_ptr(p), k.shape[0], _dev_ptr(V), _stream(stream)))
+
+
+def tfmm_planewave_noalloc(plan, khat, pol, V, stream=None):
+    """Same as tfmm_planewave, staged through the library's fixed incidence table (no allocation)."""
+    k = np.ascontiguousarray(khat, np.float64).reshape(-1, 3)
+    p = np.ascontiguousarray(pol, np.float64).reshape(-1, 3)
+    _check(load().tfmm_planewave_noalloc(plan.handle, _np_ptr(k), _np_ptr(p), k.shape[0], _dev_ptr(V),
+                                         _stream(stream)))
