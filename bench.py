@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-dense", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-groups", type=int, default=3)
+    ap.add_argument("--graph", action="store_true", help="replay one captured CUDA graph per step")
     return ap.parse_args()
 
 
@@ -63,7 +64,10 @@ def workload_desc(w, L=None, n_theta=None, n_phi=None, G=None):
          f"{w.box:g}-lambda boxes, d0={w.digits} digits")
     if L is not None:
         d += f" (L={L}, {n_theta}x{n_phi} directions, {G} groups)"
-    d += f", Tucker tol {w.tol:g}, {w.nrhs if w.rhs != 'planewave_sweep' else 1} RHS CN(0,1) seed {w.seed}"
+    if w.rhs == "planewave_sweep":
+        d += f", Tucker tol {w.tol:g}, {w.nrhs} RWG-tested plane waves theta_inc = pi i/{w.nrhs - 1}, phi_inc = 0, theta-polarised"
+    else:
+        d += f", Tucker tol {w.tol:g}, {w.nrhs} RHS CN(0,1) seed {w.seed}"
     return d
 
 
@@ -199,11 +203,12 @@ def run_reference(args, w, world, rank):
     from paper_2103_05822_gb300.inputs import complex_gaussian, icosphere
     verts, tris = icosphere(w.diameter, w.nu)
     P, pick, tuck, _ = oracle_sample(w, verts, tris, args.oracle_groups, w.seed)
-    x = complex_gaussian(P.n_rwg, w.seed)
+    R = w.nrhs
+    x = complex_gaussian((P.n_rwg, R) if R > 1 else P.n_rwg, w.seed)  # timing does not depend on the values
     ms, n = time_oracle(P, pick, tuck, x, args.steps, args.warmup)
     cores = cpu_threads()
     sample = (f"{len(pick)} of {P.groups.n_groups} groups (oracle far-field + T-HOSVD untimed); "
-              f"median of {n} steps of Tucker agg+disagg on them, scaled by groups to the whole sphere")
+              f"median of {n} steps of Tucker agg+disagg of {R} column(s) on them, scaled by groups to the whole sphere")
     line = {
         "impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
@@ -249,21 +254,32 @@ def run_ours(args, w, world, rank, local):
             import torch.distributed as dist
             dist.barrier()
 
+    R = w.nrhs
+    use_dense = not args.no_dense and R <= 8  # the dense comparator streams 16 N N_dir bytes per column
     verts, tris = icosphere(w.diameter, w.nu)
     t0 = time.perf_counter()
     mesh = tfmm.tfmm_mesh_create(verts, tris)
     prm = tfmm.tfmm_params_default(k=2 * math.pi, box=w.box, digits=float(w.digits), tol=w.tol,
-                                   keep_dense=0 if args.no_dense else 1, max_rhs=1)
+                                   keep_dense=1 if use_dense else 0, max_rhs=R)
     stream = torch.cuda.current_stream()
     plan = tfmm.tfmm_plan_create(mesh, prm, stream=stream)
     setup_s = time.perf_counter() - t0
     info = plan.info
     N, G, nd = info["n_rwg"], info["n_groups"], info["n_dir"]
 
-    x_host = complex_gaussian(N, w.seed).astype(np.complex64)
+    if w.rhs == "planewave_sweep":
+        th = np.pi * np.arange(R) / max(R - 1, 1)
+        kh = np.stack([np.sin(th), np.zeros(R), np.cos(th)], axis=1)
+        pol = np.stack([np.cos(th), np.zeros(R), -np.sin(th)], axis=1)
+        xv = torch.empty((R, N), dtype=torch.complex64, device=dev)
+        tfmm.tfmm_planewave(plan, kh, pol, xv, stream=stream)
+        torch.cuda.synchronize()
+        x_host = xv.cpu().numpy()
+    else:
+        x_host = complex_gaussian((R, N) if R > 1 else N, w.seed).astype(np.complex64)
     x = torch.from_numpy(x_host).to(dev)
-    spec = torch.empty((1, G, 2, nd), dtype=torch.complex64, device=dev)
-    y = torch.empty(N, dtype=torch.complex64, device=dev)
+    spec = torch.empty((R, G, 2, nd), dtype=torch.complex64, device=dev)
+    y = torch.empty((R, N) if R > 1 else N, dtype=torch.complex64, device=dev)
 
     def step_tucker(ev=None):
         if ev is not None:
@@ -284,6 +300,25 @@ def run_ours(args, w, world, rank, local):
         tfmm.tfmm_disaggregate_dense(plan, spec, y, stream=stream)
         if ev is not None:
             ev[2].record(stream)
+
+    graph = None
+    if args.graph:
+        step_tucker()  # first call for this R builds the chain's problem lists and scratch
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            cap = torch.cuda.current_stream()
+            tfmm.tfmm_aggregate(plan, x, spec, stream=cap)
+            tfmm.tfmm_disaggregate(plan, spec, y, stream=cap)
+        torch.cuda.synchronize()
+
+        def step_graph(ev=None):
+            if ev is not None:
+                ev[0].record(stream)
+            graph.replay()
+            if ev is not None:
+                ev[1].record(stream)
+                ev[2].record(stream)
 
     def timed(step, K, W):
         for _ in range(W):
@@ -315,8 +350,10 @@ def run_ours(args, w, world, rank, local):
         step_tucker()
     torch.cuda.synchronize()
 
-    total, agg, dis = timed(step_tucker, args.steps, args.warmup)
+    total, agg, dis = timed(step_graph if graph is not None else step_tucker, args.steps, args.warmup)
     ms_step = total / args.steps
+    if graph is not None:  # per-stage split from an eager pass
+        _, agg, dis = timed(step_tucker, args.steps, args.warmup)
     if world > 1:
         import torch.distributed as dist
         t = torch.tensor([total], device=dev)
@@ -325,22 +362,22 @@ def run_ours(args, w, world, rank, local):
     value = total / (args.steps * world)  # whole-job ms per matvec (replicas run side by side)
 
     dense = None
-    if not args.no_dense:
+    if use_dense:
         dtot, dagg, ddis = timed(step_dense, args.steps, args.warmup)
         dense = {"ms_per_matvec": dtot / args.steps, "aggregate_ms": statistics.mean(dagg),
                  "disaggregate_ms": statistics.mean(ddis)}
 
     # end to end through the host-buffer C-ABI call: H2D x, agg, disagg, D2H y, sync
     xh = torch.from_numpy(x_host).pin_memory()
-    yh = torch.empty(N, dtype=torch.complex64).pin_memory()
+    yh = torch.empty(x_host.shape, dtype=torch.complex64).pin_memory()
     for _ in range(args.warmup):
-        tfmm.tfmm_matvec_host(plan, xh, yh, stream=stream)
+        tfmm.tfmm_matvec_host(plan, xh, yh, R=R, stream=stream)
     torch.cuda.synchronize()
     barrier()
     clocks.mark(True)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        tfmm.tfmm_matvec_host(plan, xh, yh, stream=stream)
+        tfmm.tfmm_matvec_host(plan, xh, yh, R=R, stream=stream)
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
     clocks.mark(False)
     barrier()
@@ -355,30 +392,48 @@ def run_ours(args, w, world, rank, local):
         torch.cuda.synchronize()
         rel = float(torch.linalg.vector_norm(spec - ref) / torch.linalg.vector_norm(ref))
 
-    # roofline of the dominant kernel (algorithmic bytes per launch / mean launch time)
+    # roofline of the dominant kernel (algorithmic bytes or flops per launch / mean launch time)
     fac = info["tucker_bytes_alg"]
-    bytes_agg = fac + 8 * N + 16 * G * nd
-    bytes_dis = fac + 16 * G * nd + 8 * N
+    bytes_agg = fac + 8 * N * R + 16 * G * nd * R
+    bytes_dis = fac + 16 * G * nd * R + 8 * N * R
     agg_ms, dis_ms = statistics.mean(agg), statistics.mean(dis)
-    if agg_ms >= dis_ms:
-        kern, ms_k, bytes_k = "tucker_aggregate_kernel", agg_ms, bytes_agg
-    else:
-        kern, ms_k, bytes_k = "tucker_disaggregate_kernel", dis_ms, bytes_dis
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
-    peak = peaks.get("hbm_gbs", 6800.0)
-    achieved = bytes_k / (ms_k * 1e-3) / 1e9
-    roof = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-            "traffic": traffic_record(kern), "algorithmic_bytes": bytes_k}
+    if R == 1:
+        if agg_ms >= dis_ms:
+            kern, ms_k, bytes_k = "tucker_aggregate_kernel", agg_ms, bytes_agg
+        else:
+            kern, ms_k, bytes_k = "tucker_disaggregate_kernel", dis_ms, bytes_dis
+        peak = peaks.get("hbm_gbs", 6800.0)
+        achieved = bytes_k / (ms_k * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "traffic": traffic_record(kern), "algorithmic_bytes": bytes_k}
+    else:
+        # the R-column chains: complex multiply-adds of Figs. 2b / 3b, 8 real flops each
+        cm = 0
+        for g in range(G):
+            for a in range(2):
+                nb, (rt, rp, rb) = tfmm.tfmm_plan_group(plan, g, a)
+                cm += nb * rb + rt * rp * rb + info["n_phi"] * rp * rt + nd * rt
+        flops = 8.0 * cm * R
+        kern, ms_k = ("mr_gemm_kernel<AG1..AG4>", agg_ms) if agg_ms >= dis_ms else ("mr_gemm_kernel<DG1..DG3>", dis_ms)
+        sm_clock = 2.07e9
+        peak = 152 * 128 * 2 * sm_clock / 1e12  # FP32 FMA lanes x 2 flops x max SM clock
+        achieved = flops / (ms_k * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "peak_source": "FP32 CUDA cores: 152 SMs x 128 lanes x 2 flops x 2.07 GHz",
+                "traffic": None, "algorithmic_flops": flops, "algorithmic_bytes": bytes_agg}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         P, pick, tuck, _ = oracle_sample(w, verts, tris, args.oracle_groups, w.seed)
-        ms_cpu, n = time_oracle(P, pick, tuck, x_host.astype(np.complex128), 0, 1, budget_s=10.0)
+        xo = x_host.astype(np.complex128)
+        xo = xo.T if R > 1 else xo  # the oracle takes columns
+        ms_cpu, n = time_oracle(P, pick, tuck, xo, 0, 1, budget_s=10.0)
         cpu = {"value": ms_cpu, "unit": "ms", "cores": cpu_threads(), "kind": "oracle",
                "sample": f"{len(pick)} of {G} groups, oracle Tucker agg+disagg (complex128) timed {n} times "
                          f"(~10 s), median scaled by groups to the whole sphere; oracle setup untimed"}
@@ -402,8 +457,9 @@ def run_ours(args, w, world, rank, local):
             "setup_s": setup_s, "setup_ms": info["setup_ms"],
             "roofline": roof,
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N},
-            "gpu_launches": 2 * args.steps,
+            "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 8 * N * R, "d2h_bytes_per_step": 8 * N * R},
+            "gpu_launches": (2 if R == 1 else 8) * args.steps,
+            "nrhs": R, "graph": bool(args.graph),
             "clocks": clocks.summary(),
         }
         print(json.dumps(line), flush=True)

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <memory>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -71,6 +72,31 @@ struct DenseItem {
     int32_t n_beta, g, alpha, pad;
 };
 
+// Multi-RHS GEMM chain: one small complex GEMM per (group, alpha) and stage.
+struct MrProb {
+    int M, N, K, K0;       // K0: length of the first K segment (disaggregation's last stage)
+    int g, alpha, rt, rb, m, lda;
+    int64_t a0, a1;        // factor offsets (a1: second K segment)
+    int64_t b0, b1;        // input offsets (b1: second K segment)
+    int64_t c0;            // output offset
+    int64_t rwg;           // offset of the group's RWG ids
+};
+struct MrTile {
+    int prob, m0, n0;
+};
+struct MrStage {
+    MrProb* d_probs = nullptr;
+    MrTile* d_tiles = nullptr;
+    int n_tiles = 0;
+    ~MrStage();
+};
+struct MrPlan {             // per R: problem / tile lists of the 8 stages and scratch
+    int R = 0;
+    MrStage st[8];
+    float2* buf[3] = {nullptr, nullptr, nullptr};
+    ~MrPlan();
+};
+
 struct Schedule {
     int threads = 512;
     int blocks = 0;       // persistent grid
@@ -129,6 +155,8 @@ struct Plan {
     // FP64 factors (exports)
     std::vector<HostFactors64> f64;    // G x 2, pointers into f64_arenas
     std::vector<double2*> f64_arenas;  // owned device allocations
+    // multi-RHS chains, one per R used so far
+    std::vector<std::unique_ptr<MrPlan>> mr;
     // workspace of tfmm_matvec_host
     int ws_R = 0;
     float2 *d_ws_x = nullptr, *d_ws_spec = nullptr, *d_ws_y = nullptr;
@@ -153,6 +181,11 @@ void launch_dense_aggregate(const Plan& P, const float2* x, int R, int64_t ldx, 
 void launch_dense_disaggregate(const Plan& P, const float2* spec, int R, int weights, float2 beta, float2* y,
                                int64_t ldy, cudaStream_t s);
 void pack_factors_fp32(Plan& P, cudaStream_t s);  // from P.f64 into P.d_factors
+// mrhs.cu
+MrPlan* get_mr_plan(Plan& P, int R);
+void launch_mr_aggregate(Plan& P, const float2* x, int R, int64_t ldx, float2* spec, cudaStream_t s);
+void launch_mr_disaggregate(Plan& P, const float2* spec, int R, int weights, float2 beta, float2* y, int64_t ldy,
+                            cudaStream_t s);
 void pack_dense_fp32_from_f64(Plan& P, const double2* src, int g, int alpha, cudaStream_t s);
 
 inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }

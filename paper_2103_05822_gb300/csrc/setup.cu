@@ -320,176 +320,13 @@ int choose_rank(const double* ev, int n, double thr2, double tail0 = 0.0) {
 }
 
 // Batched Hermitian eigen-decomposition of `count` n x n matrices (lower part
-// valid, ld n, stride n*n) with eigenvalues ascending in W (count x n).
-// Cyclic Jacobi eigen-decomposition of small Hermitian matrices, one CTA per
-// matrix, the matrix in shared memory (Golub & Van Loan, "Matrix
-// Computations", Sec. 8.5: symmetric Schur rotations, parallel round-robin
-// ordering; the complex Hermitian case first removes the phase of a_pq).
-// G: count x n x n, lower triangle valid on entry; on exit the eigenvectors
-// (columns, ascending eigenvalues) overwrite G and W holds the eigenvalues.
-constexpr int kJacobiMax = 112;
-constexpr int kJacobiThreads = 512;
-constexpr int kJacobiSweeps = 20;
-
-__global__ void __launch_bounds__(kJacobiThreads) jacobi_eig_kernel(double2* G, double* W, int n) {
-    extern __shared__ double2 sA[];  // n x ld, column-major, ld odd (no bank conflicts on rows)
-    __shared__ double s_c[kJacobiMax / 2 + 1], s_s[kJacobiMax / 2 + 1];
-    __shared__ double2 s_e[kJacobiMax / 2 + 1];
-    __shared__ int s_p[kJacobiMax / 2 + 1], s_q[kJacobiMax / 2 + 1];
-    __shared__ double s_red[2][kJacobiThreads / 32];
-    __shared__ double s_d[kJacobiMax];
-    const int ld = n | 1, tid = threadIdx.x, NT = blockDim.x;
-    double2* V = G + (int64_t)blockIdx.x * n * n;
-    double* Wb = W + (int64_t)blockIdx.x * n;
-    for (int e = tid; e < n * n; e += NT) {
-        const int i = e % n, j = e / n;
-        double2 v;
-        if (i > j) {
-            v = V[i + (int64_t)n * j];
-        } else if (i < j) {
-            v = V[j + (int64_t)n * i];
-            v.y = -v.y;
-        } else {
-            v = make_double2(V[i + (int64_t)n * i].x, 0.0);
-        }
-        sA[i + ld * j] = v;
-    }
-    __syncthreads();
-    for (int e = tid; e < n * n; e += NT) V[e] = make_double2((e % n) == (e / n) ? 1.0 : 0.0, 0.0);
-    __syncthreads();
-    const int m = n + (n & 1);  // even number of players (one dummy when n is odd)
-    const int half = m / 2;
-    for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
-        // convergence: off-diagonal energy against the total
-        double off = 0.0, tot = 0.0;
-        for (int e = tid; e < n * n; e += NT) {
-            const int i = e % n, j = e / n;
-            const double2 v = sA[i + ld * j];
-            const double a2 = v.x * v.x + v.y * v.y;
-            tot += a2;
-            if (i != j) off += a2;
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            off += __shfl_xor_sync(0xffffffffu, off, o);
-            tot += __shfl_xor_sync(0xffffffffu, tot, o);
-        }
-        if ((tid & 31) == 0) {
-            s_red[0][tid >> 5] = off;
-            s_red[1][tid >> 5] = tot;
-        }
-        __syncthreads();
-        off = 0.0;
-        tot = 0.0;
-        for (int w = 0; w < NT / 32; ++w) {
-            off += s_red[0][w];
-            tot += s_red[1][w];
-        }
-        __syncthreads();
-        if (!(off > 1e-28 * tot)) break;  // also stops on an all-zero matrix
-        for (int step = 0; step < m - 1; ++step) {
-            if (tid < half) {
-                const int pa = tid, pb = m - 1 - tid;
-                const int a = pa == 0 ? 0 : 1 + (pa - 1 + step) % (m - 1);
-                const int b = pb == 0 ? 0 : 1 + (pb - 1 + step) % (m - 1);
-                const int p = min(a, b), q = max(a, b);
-                double c = 1.0, sn = 0.0;
-                double2 ph = make_double2(1.0, 0.0);
-                if (q < n) {
-                    const double2 apq = sA[p + ld * q];
-                    const double r = hypot(apq.x, apq.y);
-                    if (r > 0.0) {
-                        const double app = sA[p + ld * p].x, aqq = sA[q + ld * q].x;
-                        const double tau = (aqq - app) / (2.0 * r);
-                        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                        c = 1.0 / sqrt(1.0 + t * t);
-                        sn = t * c;
-                        ph = make_double2(apq.x / r, -apq.y / r);  // e^{-i phi}, a_pq = r e^{i phi}
-                    }
-                }
-                s_p[tid] = p;
-                s_q[tid] = q < n ? q : -1;
-                s_c[tid] = c;
-                s_s[tid] = sn;
-                s_e[tid] = ph;
-            }
-            __syncthreads();
-            // A <- A Q and V <- V Q, Q = [[c, s], [-s e, c e]] on columns (p, q), e = e^{-i phi}
-            for (int e = tid; e < half * n; e += NT) {
-                const int k = e / n, i = e % n;
-                const int q = s_q[k];
-                if (q < 0) continue;
-                const int p = s_p[k];
-                const double c = s_c[k], sn = s_s[k];
-                const double2 ph = s_e[k];
-                const double2 qqp = make_double2(-sn * ph.x, -sn * ph.y), qqq = make_double2(c * ph.x, c * ph.y);
-                const double2 x = sA[i + ld * p], y = sA[i + ld * q];
-                sA[i + ld * p] = make_double2(c * x.x + qqp.x * y.x - qqp.y * y.y, c * x.y + qqp.x * y.y + qqp.y * y.x);
-                sA[i + ld * q] = make_double2(sn * x.x + qqq.x * y.x - qqq.y * y.y, sn * x.y + qqq.x * y.y + qqq.y * y.x);
-                const double2 vx = V[i + (int64_t)n * p], vy = V[i + (int64_t)n * q];
-                V[i + (int64_t)n * p] =
-                    make_double2(c * vx.x + qqp.x * vy.x - qqp.y * vy.y, c * vx.y + qqp.x * vy.y + qqp.y * vy.x);
-                V[i + (int64_t)n * q] =
-                    make_double2(sn * vx.x + qqq.x * vy.x - qqq.y * vy.y, sn * vx.y + qqq.x * vy.y + qqq.y * vy.x);
-            }
-            __syncthreads();
-            // A <- Q^H A on rows (p, q)
-            for (int e = tid; e < half * n; e += NT) {
-                const int k = e / n, j = e % n;
-                const int q = s_q[k];
-                if (q < 0) continue;
-                const int p = s_p[k];
-                const double c = s_c[k], sn = s_s[k];
-                const double2 ph = s_e[k];
-                // conj(Q_qp) = -s conj(e), conj(Q_qq) = c conj(e)
-                const double2 cqp = make_double2(-sn * ph.x, sn * ph.y), cqq = make_double2(c * ph.x, -c * ph.y);
-                const double2 x = sA[p + ld * j], y = sA[q + ld * j];
-                sA[p + ld * j] = make_double2(c * x.x + cqp.x * y.x - cqp.y * y.y, c * x.y + cqp.x * y.y + cqp.y * y.x);
-                sA[q + ld * j] = make_double2(sn * x.x + cqq.x * y.x - cqq.y * y.y, sn * x.y + cqq.x * y.y + cqq.y * y.x);
-            }
-            __syncthreads();
-            // the rotated pair is diagonal up to rounding: make it exact
-            if (tid < half && s_q[tid] >= 0) {
-                const int p = s_p[tid], q = s_q[tid];
-                sA[p + ld * q] = make_double2(0.0, 0.0);
-                sA[q + ld * p] = make_double2(0.0, 0.0);
-                sA[p + ld * p].y = 0.0;
-                sA[q + ld * q].y = 0.0;
-            }
-            __syncthreads();
-        }
-    }
-    // eigenvalues ascending (ties by index), eigenvector columns permuted alike
-    for (int i = tid; i < n; i += NT) s_d[i] = sA[i + ld * i].x;
-    __syncthreads();
-    for (int e = tid; e < n * n; e += NT) {
-        const int i = e % n, j = e / n;
-        int rank = 0;
-        const double dj = s_d[j];
-        for (int k = 0; k < n; ++k) rank += (s_d[k] < dj) || (s_d[k] == dj && k < j);
-        sA[i + ld * rank] = V[i + (int64_t)n * j];
-        if (i == 0) Wb[rank] = dj;
-    }
-    __syncthreads();
-    for (int e = tid; e < n * n; e += NT) V[e] = sA[(e % n) + ld * (e / n)];
-}
-
-// Small matrices (n <= kJacobiMax): the Jacobi kernel above (TFMM_EIG=cusolver
-// disables it).  Otherwise the batched cuSOLVER solver when the library accepts the size, else one Xsyevd per
-// matrix (TFMM_EIG=single forces the latter).
+// valid, ld n, stride n*n) with eigenvalues ascending in W (count x n): the
+// batched cuSOLVER solver when the library accepts the size, else one Xsyevd
+// per matrix (TFMM_EIG=single forces the latter).
 void eig_batched(cusolverDnHandle_t sol, cusolverDnParams_t prm, double2* A, double* W, int n, int count,
                  cudaStream_t s) {
     if (count == 0) return;
     const char* env = std::getenv("TFMM_EIG");
-    if (n <= kJacobiMax && !(env && std::strcmp(env, "cusolver") == 0)) {
-        const size_t smem = sizeof(double2) * (size_t)n * (size_t)(n | 1);
-        if (smem > 48 * 1024)
-            TFMM_CUDA_CHECK(cudaFuncSetAttribute(jacobi_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem));
-        jacobi_eig_kernel<<<count, kJacobiThreads, smem, s>>>(A, W, n);
-        TFMM_CUDA_CHECK(cudaGetLastError());
-        TFMM_CUDA_CHECK(cudaStreamSynchronize(s));
-        return;
-    }
     size_t dbytes = 0, hbytes = 0;
     DevBuf info(sizeof(int) * count);
     const bool force_single = env && std::strcmp(env, "single") == 0;

@@ -3,6 +3,7 @@
 // internal errors and returns a status code.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <numeric>
@@ -174,6 +175,13 @@ void check_params(const tfmm_params& p) {
     TFMM_REQUIRE(p.quad_order >= 1 && p.quad_order <= 10, "quad_order must be in 1..10");
     TFMM_REQUIRE(p.max_rhs >= 1, "max_rhs must be >= 1");
     TFMM_REQUIRE(p.batch_groups >= 0, "batch_groups must be >= 0");
+}
+
+// R > 1 runs the grouped-GEMM chains; TFMM_MR=loop keeps the single-RHS kernels
+// looping over the columns instead (for comparisons).
+bool mr_loop_forced() {
+    const char* e = std::getenv("TFMM_MR");
+    return e && std::strcmp(e, "loop") == 0;
 }
 
 void check_hot(const Plan& P, const void* a, const void* b, int R, int64_t ld) {
@@ -497,8 +505,12 @@ tfmm_status tfmm_aggregate(tfmm_plan* plan, const tfmm_cfloat* x, int32_t R, int
     return guarded([&] {
         TFMM_REQUIRE(plan, "null plan");
         check_hot(plan->p, x, spectra, R, ldx);
-        launch_tucker_aggregate(plan->p, reinterpret_cast<const float2*>(x), R, ldx,
+        if (R > 1 && !mr_loop_forced())
+            launch_mr_aggregate(plan->p, reinterpret_cast<const float2*>(x), R, ldx,
                                 reinterpret_cast<float2*>(spectra), (cudaStream_t)stream);
+        else
+            launch_tucker_aggregate(plan->p, reinterpret_cast<const float2*>(x), R, ldx,
+                                    reinterpret_cast<float2*>(spectra), (cudaStream_t)stream);
     });
 }
 
@@ -507,9 +519,14 @@ tfmm_status tfmm_disaggregate(tfmm_plan* plan, const tfmm_cfloat* spectra, int32
     return guarded([&] {
         TFMM_REQUIRE(plan, "null plan");
         check_hot(plan->p, spectra, y, R, ldy);
-        launch_tucker_disaggregate(plan->p, reinterpret_cast<const float2*>(spectra), R, apply_weights,
+        if (R > 1 && !mr_loop_forced())
+            launch_mr_disaggregate(plan->p, reinterpret_cast<const float2*>(spectra), R, apply_weights,
                                    make_float2(beta.re, beta.im), reinterpret_cast<float2*>(y), ldy,
                                    (cudaStream_t)stream);
+        else
+            launch_tucker_disaggregate(plan->p, reinterpret_cast<const float2*>(spectra), R, apply_weights,
+                                       make_float2(beta.re, beta.im), reinterpret_cast<float2*>(y), ldy,
+                                       (cudaStream_t)stream);
     });
 }
 
@@ -558,6 +575,9 @@ tfmm_status tfmm_matvec_host(tfmm_plan* plan, const tfmm_cfloat* x_host, tfmm_cf
         if (dense) {
             launch_dense_aggregate(P, P.d_ws_x, R, P.N, P.d_ws_spec, s);
             launch_dense_disaggregate(P, P.d_ws_spec, R, 1, zero, P.d_ws_y, P.N, s);
+        } else if (R > 1 && !mr_loop_forced()) {
+            launch_mr_aggregate(P, P.d_ws_x, R, P.N, P.d_ws_spec, s);
+            launch_mr_disaggregate(P, P.d_ws_spec, R, 1, zero, P.d_ws_y, P.N, s);
         } else {
             launch_tucker_aggregate(P, P.d_ws_x, R, P.N, P.d_ws_spec, s);
             launch_tucker_disaggregate(P, P.d_ws_spec, R, 1, zero, P.d_ws_y, P.N, s);
