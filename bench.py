@@ -221,8 +221,9 @@ def run_reference(args, w, world, rank):
 
 
 # --------------------------------------------------------------------- ours
-def traffic_record(kernel):
-    """DRAM bytes per launch from a committed ncu summary, if the kernel source is unchanged since."""
+def traffic_record(kernel, factor_bytes):
+    """DRAM bytes per launch from a committed ncu capture (scaled by the factor bytes streamed),
+    if the kernel source is unchanged since."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -233,9 +234,9 @@ def traffic_record(kernel):
     src = os.path.join(ROOT, "paper_2103_05822_gb300", "csrc", "apply.cu")
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
     ent = rec.get(kernel)
-    if not ent or ent.get("apply_cu_sha256") != sha:
+    if not ent or ent.get("apply_cu_sha256") != sha or "dram_bytes_per_factor_byte" not in ent:
         return None
-    return ent.get("dram_bytes_per_launch_full")
+    return round(ent["dram_bytes_per_factor_byte"] * factor_bytes)
 
 
 def run_ours(args, w, world, rank, local):
@@ -411,7 +412,7 @@ def run_ours(args, w, world, rank, local):
         achieved = bytes_k / (ms_k * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                "traffic": traffic_record(kern), "algorithmic_bytes": bytes_k}
+                "traffic": traffic_record(kern, fac), "algorithmic_bytes": bytes_k}
     else:
         # the R-column chains: complex multiply-adds of Figs. 2b / 3b, 8 real flops each
         cm = 0
