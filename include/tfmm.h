@@ -71,7 +71,10 @@ typedef struct {
     int32_t keep_dense;/* nonzero: also keep FP32 uncompressed tensors (Eqs. 3, 5) */
     int32_t max_rhs;   /* largest R later passed to the hot path (>= 1) */
     int32_t batch_groups; /* groups per setup batch (0 = automatic) */
-    int32_t reserved[6];
+    int32_t mrhs_precision; /* R > 1: 0 = FP32 on CUDA cores; 2 or 3 = tensor cores with
+                               FP32 operands split into 2 or 3 BF16 terms (hi + lo [+ lo2]),
+                               FP32 accumulation */
+    int32_t reserved[5];
 } tfmm_params;
 
 typedef struct {
@@ -85,6 +88,8 @@ typedef struct {
     int64_t tucker_bytes_alg; /* FP32 factors + cores without padding */
     int64_t dense_bytes;      /* FP32 uncompressed tensors (0 if not kept) */
     double setup_ms[4];       /* far-field, HOSVD, packing, total */
+    int32_t kernel_errors;    /* tensor-core kernels that gave up waiting (0 when healthy) */
+    int32_t pad_;
 } tfmm_plan_info;
 
 /* Default parameters: k = 2 pi, box 0.5, 3 digits, N_phi = 2(L+1), gamma 1e-4,
@@ -147,6 +152,13 @@ tfmm_status tfmm_plan_from_tucker(int64_t n_rwg, int32_t n_groups, int32_t n_the
  * column-major tensor A[i_theta, i_phi, n] = P^{alpha,+}_{n,i} (Fig. 1a). */
 tfmm_status tfmm_plan_set_dense(tfmm_plan* plan, const tfmm_cdouble* tensors, void* stream);
 
+/* Arithmetic of the R > 1 hot path (see tfmm_params.mrhs_precision): 0, 2 or 3.
+ * Tensor-core modes build BF16 planes of the factors on first use (device
+ * memory: 2 layouts x 2 or 3 terms of every factor).  INVALID_ARG otherwise. */
+tfmm_status tfmm_plan_set_mrhs_precision(tfmm_plan* plan, int32_t precision);
+
+/* Plan sizes and setup times; also synchronises the device to read
+ * kernel_errors. */
 tfmm_status tfmm_plan_info_get(const tfmm_plan* plan, tfmm_plan_info* info);
 /* n_beta and ranks (r_theta, r_phi, r_beta) of group g, component alpha. */
 tfmm_status tfmm_plan_group(const tfmm_plan* plan, int32_t g, int32_t alpha, int64_t* n_beta,

@@ -1,6 +1,7 @@
 // Internal declarations shared by the tfmm translation units (not installed).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -97,6 +98,52 @@ struct MrPlan {             // per R: problem / tile lists of the 8 stages and s
     ~MrPlan();
 };
 
+// Tensor-core (split-BF16) multi-RHS chain.
+// Owns one device allocation (freed with its owner).
+struct DeviceBuffer {
+    void* p = nullptr;
+    DeviceBuffer() = default;
+    DeviceBuffer(const DeviceBuffer&) = delete;
+    DeviceBuffer& operator=(const DeviceBuffer&) = delete;
+    ~DeviceBuffer() {
+        if (p) cudaFree(p);
+    }
+};
+
+struct TcMat {              // 2T bfloat16 planes of one matrix, rows x ld (K-major, zero padded)
+    int64_t off = 0;
+    int64_t ld = 0;
+    int rows = 0;
+};
+struct TcItem {             // the two K-major layouts of every factor of one (group, alpha)
+    TcMat ubT, ub, c3T, c3, uphT, uph, uthT, uth;
+};
+struct TcProb {             // one grouped-GEMM problem D (M x N) = A (M x K) B (K x N), complex
+    int M, N, K0, K1, BN;   // K1 > 0: a second K segment (A1, B1)
+    const __nv_bfloat16* A0; int64_t a_ld0, a_ps0;
+    const __nv_bfloat16* B0; int64_t b_ld0, b_ps0;
+    const __nv_bfloat16* A1; int64_t a_ld1, a_ps1;
+    const __nv_bfloat16* B1; int64_t b_ld1, b_ps1;
+    void* out; int64_t o_ld, o_ps;
+    int g, alpha, rt, n_phi;
+    int64_t rwg;
+};
+struct TcStagePlan {
+    TcProb* d_probs = nullptr;
+    MrTile* d_tiles = nullptr;
+    int n_tiles = 0, n_probs = 0;
+    int max_kt = 1, max_bn = 16;  // largest K-tile count and BN over the stage's problems
+    ~TcStagePlan();
+};
+struct TcPlan {             // per (R, terms): problem lists of the 8 steps and scratch planes
+    int R = 0, T = 0;
+    TcStagePlan st[8];
+    std::vector<TcProb> host_probs[8];
+    void* last_out[8] = {};
+    void* buf[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    ~TcPlan();
+};
+
 struct Schedule {
     int threads = 512;
     int blocks = 0;       // persistent grid
@@ -157,6 +204,12 @@ struct Plan {
     std::vector<double2*> f64_arenas;  // owned device allocations
     // multi-RHS chains, one per R used so far
     std::vector<std::unique_ptr<MrPlan>> mr;
+    // tensor-core chains: factor planes (built on first use) and one chain per (R, terms)
+    int tc_terms = 0;
+    DeviceBuffer tc_fac;               // bf16 planes of every factor
+    std::vector<TcItem> tc_items;
+    DeviceBuffer tc_err;               // int: waits that gave up
+    std::vector<std::unique_ptr<TcPlan>> tc;
     // workspace of tfmm_matvec_host
     int ws_R = 0;
     float2 *d_ws_x = nullptr, *d_ws_spec = nullptr, *d_ws_y = nullptr;
@@ -181,6 +234,12 @@ void launch_dense_aggregate(const Plan& P, const float2* x, int R, int64_t ldx, 
 void launch_dense_disaggregate(const Plan& P, const float2* spec, int R, int weights, float2 beta, float2* y,
                                int64_t ldy, cudaStream_t s);
 void pack_factors_fp32(Plan& P, cudaStream_t s);  // from P.f64 into P.d_factors
+// mrhs_tc.cu
+void build_tc_factors(Plan& P, int T, cudaStream_t s);
+TcPlan* get_tc_plan(Plan& P, int R, int T, cudaStream_t s);
+void launch_tc_aggregate(Plan& P, int T, const float2* x, int R, int64_t ldx, float2* spec, cudaStream_t s);
+void launch_tc_disaggregate(Plan& P, int T, const float2* spec, int R, int weights, float2 beta, float2* y,
+                            int64_t ldy, cudaStream_t s);
 // mrhs.cu
 MrPlan* get_mr_plan(Plan& P, int R);
 void launch_mr_aggregate(Plan& P, const float2* x, int R, int64_t ldx, float2* spec, cudaStream_t s);

@@ -1,0 +1,724 @@
+// Multi-right-hand-side aggregation / disaggregation on the tensor cores
+// (tcgen05, sm_103a): the same chains as mrhs.cu (Figs. 2b, 3b with R columns),
+// every step a grouped complex GEMM D = A B with FP32 accumulation in TMEM.
+//
+// Precision.  Each FP32 operand value v is split into T bfloat16 terms
+// (T = 2: hi + lo, T = 3: hi + mid + lo; three terms represent an FP32 value
+// exactly).  A product keeps the terms whose combined order is below T:
+//   T = 2:  hi*hi + hi*lo + lo*hi
+//   T = 3:  hi*hi + hi*mid + mid*hi + hi*lo + mid*mid + lo*hi
+// and a complex product is four real ones,
+//   Cr += Ar Br - Ai Bi,   Ci += Ar Bi + Ai Br,
+// the minus sign taken by the MMA's negate-A bit.
+//
+// Layout.  An operand matrix is stored as 2T planes (re terms, then im terms)
+// of bfloat16, "K-major": row = M (or N) index, K contiguous, leading dimension
+// a multiple of 8 and zero beyond K.  A CTA computes a 128-row x BN tile
+// (BN <= 128, multiple of 16); K goes in steps of 32 through a ring of shared
+// memory stages filled by cp.async (zero-fill at ragged edges) in the
+// no-swizzle canonical layout (8 x 16-byte core matrices; the next core matrix
+// along K is 128 bytes on, the next 8 rows 512 bytes on).  One thread issues
+// the MMAs of a stage and commits them to that stage's mbarrier, which frees
+// the stage for the next load.  The epilogue reads Cr / Ci from TMEM (one row
+// per thread) and writes the next step's operand planes, or the FP32 spectra /
+// currents at the end of the chain.
+//
+// Steps (per group g and component alpha; see mrhs.cu for the FP32 version):
+//   AG1  T^T (r_b x R)            = U_beta^T . X_g          A: U_beta^T [c][n]   B: X_g   [r][n]
+//   AG2  M   (m x R)              = C_(3)^T  . T            A: C_(3)^T  [ab][c]  B: T     [r][c]
+//   AG3  V'  (r_t R x n_phi)      = M'       . U_phi^T      A: M'  [a+r_t r][b]  B: U_phi [i_phi][b]
+//   AG4  F'  (n_phi R x n_theta)  = V''      . U_theta^T    A: V'' [i_phi+n_phi r][a]  B: U_theta [i_theta][a]
+//   DG1a P'  (n_phi R x r_t)      = G'       . U_theta      A: G'  [i_phi+n_phi r][i_theta]  B: U_theta^T [a][i_theta]
+//   DG1b H'  (r_t R x r_p)        = P''      . U_phi        A: P'' [a+r_t r][i_phi]  B: U_phi^T [b][i_phi]
+//   DG2  S   (r_b x R)            = C_(3)    . H            A: C_(3) [c][ab]  B: H [r][ab]
+//   DG3  y_g (n_b x R)            = conj(U_beta^(0) S^(0) + U_beta^(1) S^(1))  A: U_beta [n][c]  B: S [r][c]
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstdlib>
+#include <vector>
+
+#include "internal.h"
+
+namespace tfmm {
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int TBM = 128;       // MMA M
+constexpr int TBK = 32;        // K per stage
+constexpr int TBN_MAX = 128;   // largest BN
+constexpr int TTHREADS = 128;  // 4 warps: one TMEM lane quarter each
+constexpr int PLANE_TILE = 8192;  // bytes of one plane tile (128 rows x 32 K x 2 B)
+constexpr long kWaitLimit = 1L << 26;
+
+enum TcStage { TAG1, TAG2, TAG3, TAG4, TDG1A, TDG1B, TDG2, TDG3 };
+
+struct TcCtx {
+    const int* grp_rwg;
+    int64_t ld;          // ldy (DG3)
+    float2 beta;         // DG3
+    int R, G, n_theta, n_dir;
+    int* err;            // set when a wait gives up
+};
+
+template <int T>
+__host__ __device__ constexpr int n_products() { return T == 2 ? 3 : 6; }
+
+// 32 consecutive TMEM columns of this warp's 32 lanes (one row per thread)
+__device__ __forceinline__ void tmem_ld32(uint32_t (&v)[32], uint32_t taddr) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t make_desc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)(128 >> 4) << 16;   // next core matrix along K
+    d |= (uint64_t)(512 >> 4) << 32;   // next 8-row group
+    d |= (uint64_t)1 << 46;            // descriptor version (sm_100 family)
+    return d;                          // base offset 0, no swizzle
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done = 0;
+    for (long it = 0; it < kWaitLimit && !done; ++it)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity));
+    return done != 0;
+}
+
+__device__ __forceinline__ void cp16(void* dst, const void* src, int bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(bytes));
+}
+
+// v = t0 + t1 (+ t2) in bfloat16 terms
+template <int T>
+__device__ __forceinline__ void split_terms(float v, bf16* t) {
+    const bf16 h = __float2bfloat16_rn(v);
+    t[0] = h;
+    const float r1 = v - __bfloat162float(h);
+    const bf16 m = __float2bfloat16_rn(r1);
+    t[1] = m;
+    if (T == 3) t[2] = __float2bfloat16_rn(r1 - __bfloat162float(m));
+}
+
+template <int T>
+__device__ __forceinline__ void store_planes(bf16* base, int64_t ps, int64_t idx, float2 v) {
+    bf16 tr[3], ti[3];
+    split_terms<T>(v.x, tr);
+    split_terms<T>(v.y, ti);
+#pragma unroll
+    for (int p = 0; p < T; ++p) {
+        base[p * ps + idx] = tr[p];
+        base[(T + p) * ps + idx] = ti[p];
+    }
+}
+
+// Loads k-tile `kt` of the problem's A (128 rows from m0) and B (BN rows from n0) into one stage.
+template <int T>
+__device__ __forceinline__ void load_stage(uint8_t* st, const TcProb& p, int m0, int n0, int kt, int kt0) {
+    const bool seg1 = kt >= kt0;
+    const int k0 = (seg1 ? kt - kt0 : kt) * TBK;
+    const int K = seg1 ? p.K1 : p.K0;
+    const int K8 = (K + 7) & ~7;
+    const bf16* A = seg1 ? p.A1 : p.A0;
+    const bf16* B = seg1 ? p.B1 : p.B0;
+    const int64_t ald = seg1 ? p.a_ld1 : p.a_ld0, aps = seg1 ? p.a_ps1 : p.a_ps0;
+    const int64_t bld = seg1 ? p.b_ld1 : p.b_ld0, bps = seg1 ? p.b_ps1 : p.b_ps0;
+    const int na = 2 * T * TBM * 4;
+    for (int idx = threadIdx.x; idx < na; idx += TTHREADS) {
+        const int pl = idx / (TBM * 4), rem = idx % (TBM * 4), r = rem >> 2, kc = rem & 3;
+        const int m = m0 + r, k = k0 + kc * 8;
+        const bool ok = m < p.M && k < K8;
+        const bf16* src = ok ? A + pl * aps + (int64_t)m * ald + k : A;
+        cp16(st + pl * PLANE_TILE + (r >> 3) * 512 + kc * 128 + (r & 7) * 16, src, ok ? 16 : 0);
+    }
+    const int nb = 2 * T * p.BN * 4;
+    uint8_t* sb = st + 2 * T * PLANE_TILE;
+    for (int idx = threadIdx.x; idx < nb; idx += TTHREADS) {
+        const int pl = idx / (p.BN * 4), rem = idx % (p.BN * 4), r = rem >> 2, kc = rem & 3;
+        const int n = n0 + r, k = k0 + kc * 8;
+        const bool ok = n < p.N && k < K8;
+        const bf16* src = ok ? B + pl * bps + (int64_t)n * bld + k : B;
+        cp16(sb + pl * PLANE_TILE + (r >> 3) * 512 + kc * 128 + (r & 7) * 16, src, ok ? 16 : 0);
+    }
+}
+
+template <int T, int S>
+__device__ __forceinline__ void epilogue(const TcCtx& c, const TcProb& p, int i, int j, float2 v) {
+    bf16* o = reinterpret_cast<bf16*>(p.out);
+    switch (S) {
+        case TAG1:  // T stored [r][c]: row j (= r), column i (= c)
+            store_planes<T>(o, p.o_ps, (int64_t)j * p.o_ld + i, v);
+            break;
+        case TAG2: {  // M' stored [a + r_t r][b]; i = a + r_t b, j = r
+            const int a = i % p.rt, b = i / p.rt;
+            store_planes<T>(o, p.o_ps, (int64_t)(a + p.rt * j) * p.o_ld + b, v);
+        } break;
+        case TAG3: {  // V'' stored [i_phi + n_phi r][a]; i = a + r_t r, j = i_phi
+            const int a = i % p.rt, r = i / p.rt;
+            store_planes<T>(o, p.o_ps, (int64_t)(j + p.n_phi * r) * p.o_ld + a, v);
+        } break;
+        case TAG4: {  // spectra; i = i_phi + n_phi r, j = i_theta
+            const int ip = i % p.n_phi, r = i / p.n_phi;
+            float2* F = reinterpret_cast<float2*>(p.out);
+            F[(((int64_t)r * c.G + p.g) * 2 + p.alpha) * c.n_dir + j + (int64_t)c.n_theta * ip] = v;
+        } break;
+        case TDG1A: {  // P'' stored [a + r_t r][i_phi]; i = i_phi + n_phi r, j = a
+            const int ip = i % p.n_phi, r = i / p.n_phi;
+            store_planes<T>(o, p.o_ps, (int64_t)(j + p.rt * r) * p.o_ld + ip, v);
+        } break;
+        case TDG1B: {  // H stored [r][a + r_t b]; i = a + r_t r, j = b
+            const int a = i % p.rt, r = i / p.rt;
+            store_planes<T>(o, p.o_ps, (int64_t)r * p.o_ld + a + p.rt * j, v);
+        } break;
+        case TDG2:  // S stored [r][c]; i = c, j = r
+            store_planes<T>(o, p.o_ps, (int64_t)j * p.o_ld + i, v);
+            break;
+        case TDG3: {  // y = beta y + conj(v); i = n, j = r
+            float2* y = reinterpret_cast<float2*>(p.out);
+            float2* dst = y + (int64_t)c.grp_rwg[p.rwg + i] + c.ld * j;
+            float2 r = make_float2(v.x, -v.y);
+            if (c.beta.x != 0.f || c.beta.y != 0.f) {
+                const float2 old = *dst;
+                r.x += c.beta.x * old.x - c.beta.y * old.y;
+                r.y += c.beta.x * old.y + c.beta.y * old.x;
+            }
+            *dst = r;
+        } break;
+    }
+}
+
+// nst: stages of the shared-memory ring (1 .. NST_MAX); tcols: TMEM columns allocated
+// (Cr at column 0, Ci at column cofs).
+template <int T, int S>
+__global__ void __launch_bounds__(TTHREADS) tc_gemm_kernel(const TcCtx c, const TcProb* __restrict__ probs,
+                                                          const MrTile* __restrict__ tiles, int nst, int tcols,
+                                                          int cofs, int hsplit) {
+    constexpr int NST_MAX = (T == 2) ? 3 : 2;
+    constexpr int STAGE = 2 * 2 * T * PLANE_TILE;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ __align__(8) uint64_t mbar[NST_MAX];
+    __shared__ uint32_t tmem_base;
+    const int NST = nst;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const MrTile t = tiles[blockIdx.x];
+    const TcProb p = probs[t.prob];
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(tcols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0)
+        for (int s = 0; s < NST; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[s])), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tm = tmem_base;
+    const int kt0 = (p.K0 + TBK - 1) / TBK;
+    const int KT = kt0 + (p.K1 > 0 ? (p.K1 + TBK - 1) / TBK : 0);
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(p.BN >> 3) << 17) | ((uint32_t)(TBM >> 4) << 24);
+    const uint32_t idesc_neg = idesc | (1u << 13);
+    bool ok = true;
+    // prologue: k-tiles 0 .. NST-2
+    for (int s = 0; s < NST - 1; ++s) {
+        if (s < KT) load_stage<T>(smem + s * STAGE, p, t.m0, t.n0, s, kt0);
+        asm volatile("cp.async.commit_group;");
+    }
+    (void)STAGE;
+    for (int kt = 0; kt < KT; ++kt) {
+        const int b = kt % NST;
+        if (NST == 1) {  // single buffer: reload it once the previous k-tile's MMAs are done
+            if (kt >= 1) ok = ok && mbar_wait(&mbar[0], (kt - 1) & 1);
+            if (ok) load_stage<T>(smem, p, t.m0, t.n0, kt, kt0);
+            asm volatile("cp.async.commit_group;");
+            asm volatile("cp.async.wait_group 0;");
+        } else if (NST == 2) {
+            asm volatile("cp.async.wait_group 0;");
+        } else {
+            asm volatile("cp.async.wait_group 1;");
+        }
+        asm volatile("fence.proxy.async.shared::cta;");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t base = smem_u32(smem + b * STAGE);
+            constexpr int PI[6] = {0, 0, 1, 0, 1, 2}, PJ[6] = {0, 1, 0, 2, 1, 0};
+#pragma unroll
+            for (int s16 = 0; s16 < 2; ++s16)
+#pragma unroll
+                for (int q = 0; q < n_products<T>(); ++q) {
+                    const uint32_t ar = base + PI[q] * PLANE_TILE + s16 * 256;
+                    const uint32_t ai = base + (T + PI[q]) * PLANE_TILE + s16 * 256;
+                    const uint32_t br = base + (2 * T + PJ[q]) * PLANE_TILE + s16 * 256;
+                    const uint32_t bi = base + (2 * T + T + PJ[q]) * PLANE_TILE + s16 * 256;
+                    // hsplit: the leading product (hi x hi) and the correction products
+                    // accumulate apart (columns 0 / 2 cofs), summed in FP32 by the epilogue
+                    const bool lo = hsplit && q > 0;
+                    const uint32_t acc = (kt > 0 || s16 > 0 || q > (lo ? 1 : 0) || (q > 0 && !hsplit)) ? 1u : 0u;
+                    const uint32_t d = tm + (lo ? 2 * cofs : 0);
+                    mma_bf16(d, make_desc(ar), make_desc(br), idesc, acc);
+                    mma_bf16(d, make_desc(ai), make_desc(bi), idesc_neg, 1u);
+                    mma_bf16(d + cofs, make_desc(ar), make_desc(bi), idesc, acc);
+                    mma_bf16(d + cofs, make_desc(ai), make_desc(br), idesc, 1u);
+                }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&mbar[b])));
+        }
+        // refill the stage that k-tile kt - 1 used, once its MMAs are done
+        if (NST > 1) {
+            const int nk = kt + NST - 1;
+            if (nk < KT) {
+                if (kt >= 1) ok = ok && mbar_wait(&mbar[(kt - 1) % NST], ((kt - 1) / NST) & 1);
+                if (ok) load_stage<T>(smem + (nk % NST) * STAGE, p, t.m0, t.n0, nk, kt0);
+            }
+            asm volatile("cp.async.commit_group;");
+        }
+    }
+    asm volatile("cp.async.wait_group 0;");
+    // always wait (bounded) for the last commit: no MMA may still read TMEM when it is freed
+    if (KT > 0 && !mbar_wait(&mbar[(KT - 1) % NST], ((KT - 1) / NST) & 1)) ok = false;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    // one verdict for the whole CTA: the TMEM loads below are warp-collective
+    ok = __syncthreads_and(ok);
+    if (!ok) {
+        if (tid == 0) atomicAdd(c.err, 1);
+    } else {
+        const int row = t.m0 + warp * 32 + lane;
+        for (int c0 = 0; c0 < p.BN; c0 += 32) {
+            uint32_t vr[32], vi[32];
+            const uint32_t ta = tm + ((uint32_t)(warp * 32) << 16) + c0;
+            tmem_ld32(vr, ta);
+            tmem_ld32(vi, ta + cofs);
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            if (hsplit) {
+                uint32_t w[32];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    tmem_ld32(w, ta + 2 * cofs + h * cofs);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;");
+                    uint32_t* v = h ? vi : vr;
+#pragma unroll
+                    for (int jj = 0; jj < 32; ++jj) v[jj] = __float_as_uint(__uint_as_float(v[jj]) + __uint_as_float(w[jj]));
+                }
+            }
+            if (row < p.M) {
+#pragma unroll 8
+                for (int jj = 0; jj < 32; ++jj) {
+                    const int col = t.n0 + c0 + jj;
+                    if (c0 + jj < p.BN && col < p.N)
+                        epilogue<T, S>(c, p, row, col, make_float2(__uint_as_float(vr[jj]), __uint_as_float(vi[jj])));
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(tcols));
+}
+
+// ------------------------------------------------------------ operand prep
+// Split planes of an FP32 complex matrix: dst[p][r][k] for r < rows, k < cols,
+// src element (r, k) at src[r * sr + k * sk]; entries k in [cols, ld) stay as they are.
+template <int T>
+__global__ void planes_kernel(const float2* __restrict__ src, int rows, int cols, int64_t sr, int64_t sk,
+                              bf16* __restrict__ dst, int64_t ld, int64_t ps) {
+    const int64_t total = (int64_t)rows * cols;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / cols), k = (int)(e % cols);
+        store_planes<T>(dst, ps, (int64_t)r * ld + k, src[(int64_t)r * sr + (int64_t)k * sk]);
+    }
+}
+
+// X_g planes [r][n] for every group: x[grp_rwg[off_g + n] + ldx r].
+template <int T>
+__global__ void prep_x_kernel(const float2* __restrict__ x, int64_t ldx, const int* __restrict__ grp_rwg,
+                              const TcProb* __restrict__ probs, int n_probs, int R) {
+    for (int q = blockIdx.y; q < n_probs; q += gridDim.y) {
+        const TcProb& p = probs[q];  // AG1 problem of (g, alpha = 0): B0 points at the group's X planes
+        if (p.alpha != 0) continue;
+        bf16* dst = const_cast<bf16*>(p.B0);
+        const int nb = p.K0;
+        const int64_t total = (int64_t)R * nb;
+        for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+            const int r = (int)(e / nb), n = (int)(e % nb);
+            store_planes<T>(dst, p.b_ps0, (int64_t)r * p.b_ld0 + n, x[(int64_t)grp_rwg[p.rwg + n] + ldx * r]);
+        }
+    }
+}
+
+// G' planes [i_phi + n_phi r][i_theta] = conj(W g) for every (g, alpha).
+template <int T>
+__global__ void prep_g_kernel(const float2* __restrict__ spec, const float* __restrict__ w,
+                              const TcProb* __restrict__ probs, int n_probs, int R, int G, int n_theta, int n_phi) {
+    const int n_dir = n_theta * n_phi;
+    for (int q = blockIdx.y; q < n_probs; q += gridDim.y) {
+        const TcProb& p = probs[q];  // DG1a problem: A0 points at the item's G' planes
+        bf16* dst = const_cast<bf16*>(p.A0);
+        const int64_t total = (int64_t)R * n_dir;
+        for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+            const int r = (int)(e / n_dir), o = (int)(e % n_dir);
+            const int it = o % n_theta, ip = o / n_theta;
+            const float2 v = spec[(((int64_t)r * G + p.g) * 2 + p.alpha) * n_dir + o];
+            const float wt = w ? w[o] : 1.0f;
+            store_planes<T>(dst, p.a_ps0, (int64_t)(ip + n_phi * r) * p.a_ld0 + it, make_float2(wt * v.x, -wt * v.y));
+        }
+    }
+}
+
+int g1d(int64_t total) { return (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 4096)); }
+
+int64_t r8(int64_t v) { return (v + 7) & ~int64_t(7); }
+
+// Leading and correction products in separate TMEM accumulators (TFMM_TC_HSPLIT=0 turns it off).
+bool tc_split_accumulators() {
+    static const bool on = [] {
+        const char* e = std::getenv("TFMM_TC_HSPLIT");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
+// Ring depth and TMEM columns from the stage's largest K and BN; shared memory is
+// padded so that the CTAs one SM can hold never ask for more than its 512 columns.
+template <int T, int S>
+void launch_tc(const TcStagePlan& st, const TcCtx& c, cudaStream_t s) {
+    if (st.n_tiles == 0) return;
+    constexpr int NST_MAX = (T == 2) ? 3 : 2;
+    constexpr size_t STAGE = (size_t)2 * 2 * T * PLANE_TILE;
+    const int nst = std::max(1, std::min(NST_MAX, st.max_kt));
+    const int cofs = (st.max_bn + 31) / 32 * 32;
+    const int hsplit = tc_split_accumulators() ? 1 : 0;
+    int tcols = 32;
+    while (tcols < (hsplit ? 4 : 2) * cofs) tcols *= 2;
+    // at most 512 / tcols CTAs per SM: pad the shared memory request so that no more fit
+    const int ctas_tmem = 512 / tcols;
+    constexpr size_t kSmemSM = 228 * 1024, kMaxDyn = 225 * 1024;
+    size_t smem = nst * STAGE;
+    if (kSmemSM / (smem + 2048) > (size_t)ctas_tmem) smem = std::min(kMaxDyn, kSmemSM / ctas_tmem - 2048);
+    static bool attr = false;
+    if (!attr) {
+        TFMM_CUDA_CHECK(cudaFuncSetAttribute(tc_gemm_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kMaxDyn));
+        attr = true;
+    }
+    tc_gemm_kernel<T, S><<<st.n_tiles, TTHREADS, smem, s>>>(c, reinterpret_cast<const TcProb*>(st.d_probs), st.d_tiles,
+                                                             nst, tcols, cofs, hsplit);
+    TFMM_CUDA_CHECK(cudaGetLastError());
+}
+
+}  // namespace
+
+TcStagePlan::~TcStagePlan() {
+    if (d_probs) cudaFree(d_probs);
+    if (d_tiles) cudaFree(d_tiles);
+}
+
+TcPlan::~TcPlan() {
+    for (auto* b : buf)
+        if (b) cudaFree(b);
+}
+
+// BF16 planes of every factor in the two K-major layouts the chains read.
+void build_tc_factors(Plan& P, int T, cudaStream_t s) {
+    if (P.tc_terms == T && P.tc_fac.p) return;
+    if (P.tc_fac.p) cudaFree(P.tc_fac.p);
+    P.tc_fac.p = nullptr;
+    P.tc_terms = T;
+    const int nt = P.n_theta, np = P.n_phi;
+    P.tc_items.assign(P.items.size(), TcItem{});
+    int64_t off = 0;
+    auto add = [&](TcMat& m, int rows, int cols) {
+        m.rows = rows;
+        m.ld = r8(cols);
+        m.off = off;
+        off += (int64_t)2 * T * rows * m.ld;
+        off = (off + 63) & ~int64_t(63);
+    };
+    for (size_t q = 0; q < P.items.size(); ++q) {
+        const TuckerItem& d = P.items[q];
+        TcItem& t = P.tc_items[q];
+        const int m = d.rt * d.rp;
+        add(t.ubT, d.rb, d.n_beta);   // [c][n]
+        add(t.ub, d.n_beta, d.rb);    // [n][c]
+        add(t.c3T, m, d.rb);          // [ab][c]
+        add(t.c3, d.rb, m);           // [c][ab]
+        add(t.uphT, np, d.rp);        // [i_phi][b]
+        add(t.uph, d.rp, np);         // [b][i_phi]
+        add(t.uthT, nt, d.rt);        // [i_theta][a]
+        add(t.uth, d.rt, nt);         // [a][i_theta]
+    }
+    TFMM_CUDA_CHECK(cudaMalloc(&P.tc_fac.p, sizeof(bf16) * std::max<int64_t>(off, 1)));
+    TFMM_CUDA_CHECK(cudaMemsetAsync(P.tc_fac.p, 0, sizeof(bf16) * std::max<int64_t>(off, 1), s));
+    bf16* base = reinterpret_cast<bf16*>(P.tc_fac.p);
+    auto conv = [&](const float2* src, int rows, int cols, int64_t sr, int64_t sk, const TcMat& m) {
+        const int64_t ps = (int64_t)m.rows * m.ld;
+        if (T == 2)
+            planes_kernel<2><<<g1d((int64_t)rows * cols), 256, 0, s>>>(src, rows, cols, sr, sk, base + m.off, m.ld, ps);
+        else
+            planes_kernel<3><<<g1d((int64_t)rows * cols), 256, 0, s>>>(src, rows, cols, sr, sk, base + m.off, m.ld, ps);
+    };
+    for (size_t q = 0; q < P.items.size(); ++q) {
+        const TuckerItem& d = P.items[q];
+        const TcItem& t = P.tc_items[q];
+        const int m = d.rt * d.rp;
+        const float2* ub = P.d_factors + d.ub;      // U_beta^T rows: (c, n) at c ld_nb + n
+        const float2* cc = P.d_factors + d.core;    // C_(3) rows:    (c, ab) at c ld_ab + ab
+        const float2* up = P.d_factors + d.uphi;    // U_phi:         (i_phi, b) at i_phi + n_phi b
+        const float2* ut = P.d_factors + d.uth;     // U_theta:       (i_theta, a) at i_theta + n_theta a
+        conv(ub, d.rb, d.n_beta, d.ld_nb, 1, t.ubT);
+        conv(ub, d.n_beta, d.rb, 1, d.ld_nb, t.ub);
+        conv(cc, m, d.rb, 1, d.ld_ab, t.c3T);
+        conv(cc, d.rb, m, d.ld_ab, 1, t.c3);
+        conv(up, np, d.rp, 1, np, t.uphT);
+        conv(up, d.rp, np, np, 1, t.uph);
+        conv(ut, nt, d.rt, 1, nt, t.uthT);
+        conv(ut, d.rt, nt, nt, 1, t.uth);
+    }
+    TFMM_CUDA_CHECK(cudaGetLastError());
+    TFMM_CUDA_CHECK(cudaStreamSynchronize(s));
+    if (!P.tc_err.p) {
+        TFMM_CUDA_CHECK(cudaMalloc(&P.tc_err.p, sizeof(int)));
+        TFMM_CUDA_CHECK(cudaMemset(P.tc_err.p, 0, sizeof(int)));
+    }
+}
+
+namespace {
+
+void add_tc_tiles(std::vector<MrTile>& tiles, int prob, int M, int N) {
+    for (int m0 = 0; m0 < M; m0 += TBM)
+        for (int n0 = 0; n0 < N; n0 += TBN_MAX) tiles.push_back(MrTile{prob, m0, n0});
+}
+
+int bn_of(int N) { return (int)std::min<int64_t>(TBN_MAX, (N + 15) / 16 * 16); }
+
+void upload_tc_stage(TcStagePlan& st, const std::vector<TcProb>& probs, const std::vector<MrTile>& tiles) {
+    st.n_tiles = (int)tiles.size();
+    st.n_probs = (int)probs.size();
+    st.max_kt = 1;
+    st.max_bn = 16;
+    for (const auto& p : probs) {
+        const int kt = (p.K0 + TBK - 1) / TBK + (p.K1 > 0 ? (p.K1 + TBK - 1) / TBK : 0);
+        st.max_kt = std::max(st.max_kt, kt);
+        st.max_bn = std::max(st.max_bn, p.BN);
+    }
+    TFMM_CUDA_CHECK(cudaMalloc(&st.d_probs, sizeof(TcProb) * std::max<size_t>(probs.size(), 1)));
+    TFMM_CUDA_CHECK(cudaMalloc(&st.d_tiles, sizeof(MrTile) * std::max<size_t>(tiles.size(), 1)));
+    TFMM_CUDA_CHECK(cudaMemcpy(st.d_probs, probs.data(), sizeof(TcProb) * probs.size(), cudaMemcpyHostToDevice));
+    TFMM_CUDA_CHECK(cudaMemcpy(st.d_tiles, tiles.data(), sizeof(MrTile) * tiles.size(), cudaMemcpyHostToDevice));
+}
+
+}  // namespace
+
+TcPlan* get_tc_plan(Plan& P, int R, int T, cudaStream_t s) {
+    build_tc_factors(P, T, s);
+    for (auto& m : P.tc)
+        if (m->R == R && m->T == T) return m.get();
+    auto tp = std::make_unique<TcPlan>();
+    TcPlan& M = *tp;
+    M.R = R;
+    M.T = T;
+    const int nt = P.n_theta, np = P.n_phi;
+    const int nI = P.G * 2;
+    const bf16* F = reinterpret_cast<const bf16*>(P.tc_fac.p);
+    // scratch planes: X (per group), T/S, M'/H, V''/P'', G' (per item)
+    enum { BX, BT, BM, BV, BG, NB };
+    int64_t sz[NB] = {0, 0, 0, 0, 0};
+    struct Off { int64_t x, t, m, v, g; int64_t ldt, ldm, ldv, ldg, ldx; };
+    std::vector<Off> of(nI);
+    for (int q = 0; q < nI; ++q) {
+        const TuckerItem& d = P.items[q];
+        const int m = d.rt * d.rp;
+        Off& o = of[q];
+        o.ldx = r8(d.n_beta);
+        if (d.alpha == 0) { o.x = sz[BX]; sz[BX] += (int64_t)2 * T * R * o.ldx; }
+        else o.x = of[q - 1].x;
+        // T ([r][c]) and S ([r][c]) share a buffer
+        o.ldt = r8(d.rb); o.t = sz[BT]; sz[BT] += (int64_t)2 * T * R * o.ldt;
+        // M' ([a + r_t r][b]) and H ([r][a + r_t b]) share a buffer
+        o.ldm = std::max(r8(d.rp), r8(m));
+        o.m = sz[BM]; sz[BM] += (int64_t)2 * T * std::max<int64_t>((int64_t)d.rt * R * r8(d.rp), (int64_t)R * r8(m));
+        // V'' ([i_phi + n_phi r][a]) and P'' ([a + r_t r][i_phi]) share a buffer
+        o.v = sz[BV]; sz[BV] += (int64_t)2 * T * std::max<int64_t>((int64_t)np * R * r8(d.rt), (int64_t)d.rt * R * r8(np));
+        o.ldg = r8(nt); o.g = sz[BG]; sz[BG] += (int64_t)2 * T * np * R * o.ldg;
+        for (int b = 0; b < NB; ++b) sz[b] = (sz[b] + 63) & ~int64_t(63);
+    }
+    for (int b = 0; b < NB; ++b) {
+        TFMM_CUDA_CHECK(cudaMalloc(&M.buf[b], sizeof(bf16) * std::max<int64_t>(sz[b], 1)));
+        TFMM_CUDA_CHECK(cudaMemset(M.buf[b], 0, sizeof(bf16) * std::max<int64_t>(sz[b], 1)));
+    }
+    bf16* X = reinterpret_cast<bf16*>(M.buf[BX]);
+    bf16* Tb = reinterpret_cast<bf16*>(M.buf[BT]);
+    bf16* Mb = reinterpret_cast<bf16*>(M.buf[BM]);
+    bf16* Vb = reinterpret_cast<bf16*>(M.buf[BV]);
+    bf16* Gb = reinterpret_cast<bf16*>(M.buf[BG]);
+    std::vector<TcProb> pr[8];
+    std::vector<MrTile> tl[8];
+    for (int q = 0; q < nI; ++q) {
+        const TuckerItem& d = P.items[q];
+        const TcItem& f = P.tc_items[q];
+        const Off& o = of[q];
+        const int m = d.rt * d.rp;
+        TcProb b{};
+        b.g = d.g; b.alpha = d.alpha; b.rt = d.rt; b.n_phi = np; b.rwg = d.rwg;
+        auto mat = [&](const TcMat& t, const bf16*& ptr, int64_t& ld, int64_t& ps) {
+            ptr = F + t.off; ld = t.ld; ps = (int64_t)t.rows * t.ld;
+        };
+        // AG1: T^T = U_beta^T X_g ; out T planes [r][c]
+        TcProb p = b;
+        p.M = d.rb; p.N = R; p.K0 = d.n_beta; p.BN = bn_of(R);
+        mat(f.ubT, p.A0, p.a_ld0, p.a_ps0);
+        p.B0 = X + o.x; p.b_ld0 = o.ldx; p.b_ps0 = (int64_t)R * o.ldx;
+        p.out = Tb + o.t; p.o_ld = o.ldt; p.o_ps = (int64_t)R * o.ldt;
+        add_tc_tiles(tl[TAG1], (int)pr[TAG1].size(), p.M, p.N); pr[TAG1].push_back(p);
+        // AG2: M = C_(3)^T T ; out M' planes [a + r_t r][b]
+        p = b;
+        p.M = m; p.N = R; p.K0 = d.rb; p.BN = bn_of(R);
+        mat(f.c3T, p.A0, p.a_ld0, p.a_ps0);
+        p.B0 = Tb + o.t; p.b_ld0 = o.ldt; p.b_ps0 = (int64_t)R * o.ldt;
+        p.out = Mb + o.m; p.o_ld = r8(d.rp); p.o_ps = (int64_t)d.rt * R * r8(d.rp);
+        add_tc_tiles(tl[TAG2], (int)pr[TAG2].size(), p.M, p.N); pr[TAG2].push_back(p);
+        // AG3: V' = M' U_phi^T ; out V'' planes [i_phi + n_phi r][a]
+        p = b;
+        p.M = d.rt * R; p.N = np; p.K0 = d.rp; p.BN = bn_of(np);
+        p.A0 = Mb + o.m; p.a_ld0 = r8(d.rp); p.a_ps0 = (int64_t)d.rt * R * r8(d.rp);
+        mat(f.uphT, p.B0, p.b_ld0, p.b_ps0);
+        p.out = Vb + o.v; p.o_ld = r8(d.rt); p.o_ps = (int64_t)np * R * r8(d.rt);
+        add_tc_tiles(tl[TAG3], (int)pr[TAG3].size(), p.M, p.N); pr[TAG3].push_back(p);
+        // AG4: F' = V'' U_theta^T ; out spectra (set at launch)
+        p = b;
+        p.M = np * R; p.N = nt; p.K0 = d.rt; p.BN = bn_of(nt);
+        p.A0 = Vb + o.v; p.a_ld0 = r8(d.rt); p.a_ps0 = (int64_t)np * R * r8(d.rt);
+        mat(f.uthT, p.B0, p.b_ld0, p.b_ps0);
+        add_tc_tiles(tl[TAG4], (int)pr[TAG4].size(), p.M, p.N); pr[TAG4].push_back(p);
+        // DG1a: P' = G' U_theta ; out P'' planes [a + r_t r][i_phi]
+        p = b;
+        p.M = np * R; p.N = d.rt; p.K0 = nt; p.BN = bn_of(d.rt);
+        p.A0 = Gb + o.g; p.a_ld0 = o.ldg; p.a_ps0 = (int64_t)np * R * o.ldg;
+        mat(f.uth, p.B0, p.b_ld0, p.b_ps0);
+        p.out = Vb + o.v; p.o_ld = r8(np); p.o_ps = (int64_t)d.rt * R * r8(np);
+        add_tc_tiles(tl[TDG1A], (int)pr[TDG1A].size(), p.M, p.N); pr[TDG1A].push_back(p);
+        // DG1b: H' = P'' U_phi ; out H planes [r][a + r_t b]
+        p = b;
+        p.M = d.rt * R; p.N = d.rp; p.K0 = np; p.BN = bn_of(d.rp);
+        p.A0 = Vb + o.v; p.a_ld0 = r8(np); p.a_ps0 = (int64_t)d.rt * R * r8(np);
+        mat(f.uph, p.B0, p.b_ld0, p.b_ps0);
+        p.out = Mb + o.m; p.o_ld = r8(m); p.o_ps = (int64_t)R * r8(m);
+        add_tc_tiles(tl[TDG1B], (int)pr[TDG1B].size(), p.M, p.N); pr[TDG1B].push_back(p);
+        // DG2: S = C_(3) H ; out S planes [r][c]
+        p = b;
+        p.M = d.rb; p.N = R; p.K0 = m; p.BN = bn_of(R);
+        mat(f.c3, p.A0, p.a_ld0, p.a_ps0);
+        p.B0 = Mb + o.m; p.b_ld0 = r8(m); p.b_ps0 = (int64_t)R * r8(m);
+        p.out = Tb + o.t; p.o_ld = o.ldt; p.o_ps = (int64_t)R * o.ldt;
+        add_tc_tiles(tl[TDG2], (int)pr[TDG2].size(), p.M, p.N); pr[TDG2].push_back(p);
+    }
+    for (int g = 0; g < P.G; ++g) {
+        const TuckerItem& d0 = P.items[2 * g];
+        const TuckerItem& d1 = P.items[2 * g + 1];
+        TcProb p{};
+        p.g = g; p.rwg = d0.rwg;
+        p.M = d0.n_beta; p.N = R; p.K0 = d0.rb; p.K1 = d1.rb; p.BN = bn_of(R);
+        const TcMat& u0 = P.tc_items[2 * g].ub;
+        const TcMat& u1 = P.tc_items[2 * g + 1].ub;
+        p.A0 = F + u0.off; p.a_ld0 = u0.ld; p.a_ps0 = (int64_t)u0.rows * u0.ld;
+        p.A1 = F + u1.off; p.a_ld1 = u1.ld; p.a_ps1 = (int64_t)u1.rows * u1.ld;
+        p.B0 = Tb + of[2 * g].t; p.b_ld0 = of[2 * g].ldt; p.b_ps0 = (int64_t)R * of[2 * g].ldt;
+        p.B1 = Tb + of[2 * g + 1].t; p.b_ld1 = of[2 * g + 1].ldt; p.b_ps1 = (int64_t)R * of[2 * g + 1].ldt;
+        add_tc_tiles(tl[TDG3], (int)pr[TDG3].size(), p.M, p.N); pr[TDG3].push_back(p);
+    }
+    for (int st = 0; st < 8; ++st) {
+        M.host_probs[st] = pr[st];
+        upload_tc_stage(M.st[st], pr[st], tl[st]);
+    }
+    P.tc.push_back(std::move(tp));
+    return P.tc.back().get();
+}
+
+namespace {
+
+// Output pointers that change per call (spectra, y) are patched into the problem lists.
+// (stream-ordered: earlier launches on the stream still read the old list)
+void set_outputs(TcPlan& M, int stage, void* out, cudaStream_t s) {
+    if (M.last_out[stage] == out) return;
+    std::vector<TcProb>& v = M.host_probs[stage];
+    for (auto& p : v) p.out = out;
+    TFMM_CUDA_CHECK(cudaMemcpyAsync(M.st[stage].d_probs, v.data(), sizeof(TcProb) * v.size(), cudaMemcpyHostToDevice, s));
+    TFMM_CUDA_CHECK(cudaStreamSynchronize(s));  // the host list may change again on the next call
+    M.last_out[stage] = out;
+}
+
+template <int T>
+void tc_aggregate_t(Plan& P, TcPlan& M, const float2* x, int R, int64_t ldx, float2* spec, cudaStream_t s) {
+    TcCtx c{};
+    c.grp_rwg = P.d_grp_rwg; c.R = R; c.G = P.G; c.n_theta = P.n_theta; c.n_dir = P.n_dir; c.err = static_cast<int*>(P.tc_err.p);
+    set_outputs(M, TAG4, spec, s);
+    dim3 gx(64, std::min(P.G * 2, 4096));
+    prep_x_kernel<T><<<gx, 256, 0, s>>>(x, ldx, P.d_grp_rwg, reinterpret_cast<const TcProb*>(M.st[TAG1].d_probs),
+                                        M.st[TAG1].n_probs, R);
+    TFMM_CUDA_CHECK(cudaGetLastError());
+    launch_tc<T, TAG1>(M.st[TAG1], c, s);
+    launch_tc<T, TAG2>(M.st[TAG2], c, s);
+    launch_tc<T, TAG3>(M.st[TAG3], c, s);
+    launch_tc<T, TAG4>(M.st[TAG4], c, s);
+}
+
+template <int T>
+void tc_disaggregate_t(Plan& P, TcPlan& M, const float2* spec, int R, int weights, float2 beta, float2* y,
+                       int64_t ldy, cudaStream_t s) {
+    TcCtx c{};
+    c.grp_rwg = P.d_grp_rwg; c.R = R; c.G = P.G; c.n_theta = P.n_theta; c.n_dir = P.n_dir; c.err = static_cast<int*>(P.tc_err.p);
+    c.ld = ldy; c.beta = beta;
+    set_outputs(M, TDG3, y, s);
+    dim3 gg(64, std::min(P.G * 2, 4096));
+    prep_g_kernel<T><<<gg, 256, 0, s>>>(spec, weights ? P.d_weights : nullptr,
+                                        reinterpret_cast<const TcProb*>(M.st[TDG1A].d_probs), M.st[TDG1A].n_probs, R,
+                                        P.G, P.n_theta, P.n_phi);
+    TFMM_CUDA_CHECK(cudaGetLastError());
+    launch_tc<T, TDG1A>(M.st[TDG1A], c, s);
+    launch_tc<T, TDG1B>(M.st[TDG1B], c, s);
+    launch_tc<T, TDG2>(M.st[TDG2], c, s);
+    launch_tc<T, TDG3>(M.st[TDG3], c, s);
+}
+
+}  // namespace
+
+void launch_tc_aggregate(Plan& P, int T, const float2* x, int R, int64_t ldx, float2* spec, cudaStream_t s) {
+    TcPlan* M = get_tc_plan(P, R, T, s);
+    if (T == 2)
+        tc_aggregate_t<2>(P, *M, x, R, ldx, spec, s);
+    else
+        tc_aggregate_t<3>(P, *M, x, R, ldx, spec, s);
+}
+
+void launch_tc_disaggregate(Plan& P, int T, const float2* spec, int R, int weights, float2 beta, float2* y,
+                            int64_t ldy, cudaStream_t s) {
+    TcPlan* M = get_tc_plan(P, R, T, s);
+    if (T == 2)
+        tc_disaggregate_t<2>(P, *M, spec, R, weights, beta, y, ldy, s);
+    else
+        tc_disaggregate_t<3>(P, *M, spec, R, weights, beta, y, ldy, s);
+}
+
+}  // namespace tfmm

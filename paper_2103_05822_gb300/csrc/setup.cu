@@ -188,28 +188,6 @@ __global__ void take_top_kernel(const double2* __restrict__ G, int ldg, int n, i
     }
 }
 
-// Pads an n x n Gram matrix (lower part valid) into an nb x nb buffer: zeros off
-// the block, `diag` on the padded diagonal (below every true eigenvalue).
-__global__ void pad_gram_kernel(double2* __restrict__ G, int n, int nb, double diag) {
-    const int64_t total = (int64_t)nb * nb;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(e % nb), j = (int)(e / nb);
-        if (i < n && j < n) continue;
-        G[e] = make_double2(i == j ? diag : 0.0, 0.0);
-    }
-}
-
-// Copies an n x n lower triangle from src (ld n) into dst (ld nb).
-__global__ void copy_lower_kernel(const double2* __restrict__ src, int n, double2* __restrict__ dst, int nb) {
-    const int64_t total = (int64_t)n * n;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(e % n), j = (int)(e / n);
-        if (i >= j) dst[i + (int64_t)nb * j] = src[e];
-    }
-}
-
 // FP64 -> FP32 copy of an n x m column-major block into a buffer with leading dimension ldo.
 __global__ void to_f32_kernel(const double2* __restrict__ in, int64_t n, int64_t m, int64_t ldi,
                               float2* __restrict__ out, int64_t ldo) {
@@ -807,7 +785,7 @@ void build_tucker_setup(Plan& P, const Mesh& M, cudaStream_t s) {
     (void)M;
     const auto t_all = std::chrono::steady_clock::now();
     const tfmm_params& prm = P.params;
-    const int nt = P.n_theta, np = P.n_phi, nd = P.n_dir;
+    const int nd = P.n_dir;
     const bool keep_dense = prm.keep_dense != 0;
     TFMM_REQUIRE(prm.quad_order >= 1 && prm.quad_order <= kMaxQuad, "quad_order must be in 1..10");
     upload_quadrature(prm.quad_order, s);

@@ -175,6 +175,8 @@ void check_params(const tfmm_params& p) {
     TFMM_REQUIRE(p.quad_order >= 1 && p.quad_order <= 10, "quad_order must be in 1..10");
     TFMM_REQUIRE(p.max_rhs >= 1, "max_rhs must be >= 1");
     TFMM_REQUIRE(p.batch_groups >= 0, "batch_groups must be >= 0");
+    TFMM_REQUIRE(p.mrhs_precision == 0 || p.mrhs_precision == 2 || p.mrhs_precision == 3,
+                 "mrhs_precision must be 0, 2 or 3");
 }
 
 // R > 1 runs the grouped-GEMM chains; TFMM_MR=loop keeps the single-RHS kernels
@@ -182,6 +184,13 @@ void check_params(const tfmm_params& p) {
 bool mr_loop_forced() {
     const char* e = std::getenv("TFMM_MR");
     return e && std::strcmp(e, "loop") == 0;
+}
+
+// Split-BF16 terms of the tensor-core chain for this call (0: FP32 CUDA-core chain).
+int tc_terms_for(const Plan& P, int R) {
+    if (R <= 1 || mr_loop_forced()) return 0;
+    const int p = P.params.mrhs_precision;
+    return (p == 2 || p == 3) ? p : 0;
 }
 
 void check_hot(const Plan& P, const void* a, const void* b, int R, int64_t ld) {
@@ -426,6 +435,15 @@ tfmm_status tfmm_plan_info_get(const tfmm_plan* plan, tfmm_plan_info* info) {
         info->tucker_bytes_alg = P.factor_elems_alg * (int64_t)sizeof(float2);
         info->dense_bytes = P.d_dense ? P.dense_elems * (int64_t)sizeof(float2) : 0;
         for (int c = 0; c < 4; ++c) info->setup_ms[c] = P.setup_ms[c];
+        if (P.tc_err.p) TFMM_CUDA_CHECK(cudaMemcpy(&info->kernel_errors, P.tc_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+    });
+}
+
+tfmm_status tfmm_plan_set_mrhs_precision(tfmm_plan* plan, int32_t precision) {
+    return guarded([&] {
+        TFMM_REQUIRE(plan, "null plan");
+        TFMM_REQUIRE(precision == 0 || precision == 2 || precision == 3, "mrhs_precision must be 0, 2 or 3");
+        plan->p.params.mrhs_precision = precision;
     });
 }
 
@@ -505,7 +523,10 @@ tfmm_status tfmm_aggregate(tfmm_plan* plan, const tfmm_cfloat* x, int32_t R, int
     return guarded([&] {
         TFMM_REQUIRE(plan, "null plan");
         check_hot(plan->p, x, spectra, R, ldx);
-        if (R > 1 && !mr_loop_forced())
+        if (const int T = tc_terms_for(plan->p, R))
+            launch_tc_aggregate(plan->p, T, reinterpret_cast<const float2*>(x), R, ldx,
+                                reinterpret_cast<float2*>(spectra), (cudaStream_t)stream);
+        else if (R > 1 && !mr_loop_forced())
             launch_mr_aggregate(plan->p, reinterpret_cast<const float2*>(x), R, ldx,
                                 reinterpret_cast<float2*>(spectra), (cudaStream_t)stream);
         else
@@ -519,7 +540,11 @@ tfmm_status tfmm_disaggregate(tfmm_plan* plan, const tfmm_cfloat* spectra, int32
     return guarded([&] {
         TFMM_REQUIRE(plan, "null plan");
         check_hot(plan->p, spectra, y, R, ldy);
-        if (R > 1 && !mr_loop_forced())
+        if (const int T = tc_terms_for(plan->p, R))
+            launch_tc_disaggregate(plan->p, T, reinterpret_cast<const float2*>(spectra), R, apply_weights,
+                                   make_float2(beta.re, beta.im), reinterpret_cast<float2*>(y), ldy,
+                                   (cudaStream_t)stream);
+        else if (R > 1 && !mr_loop_forced())
             launch_mr_disaggregate(plan->p, reinterpret_cast<const float2*>(spectra), R, apply_weights,
                                    make_float2(beta.re, beta.im), reinterpret_cast<float2*>(y), ldy,
                                    (cudaStream_t)stream);
@@ -575,6 +600,9 @@ tfmm_status tfmm_matvec_host(tfmm_plan* plan, const tfmm_cfloat* x_host, tfmm_cf
         if (dense) {
             launch_dense_aggregate(P, P.d_ws_x, R, P.N, P.d_ws_spec, s);
             launch_dense_disaggregate(P, P.d_ws_spec, R, 1, zero, P.d_ws_y, P.N, s);
+        } else if (const int T = tc_terms_for(P, R)) {
+            launch_tc_aggregate(P, T, P.d_ws_x, R, P.N, P.d_ws_spec, s);
+            launch_tc_disaggregate(P, T, P.d_ws_spec, R, 1, zero, P.d_ws_y, P.N, s);
         } else if (R > 1 && !mr_loop_forced()) {
             launch_mr_aggregate(P, P.d_ws_x, R, P.N, P.d_ws_spec, s);
             launch_mr_disaggregate(P, P.d_ws_spec, R, 1, zero, P.d_ws_y, P.N, s);

@@ -25,7 +25,7 @@ EXPORTED = [
     "tfmm_plan_group", "tfmm_plan_members", "tfmm_plan_centres", "tfmm_plan_quadrature",
     "tfmm_plan_export_factors", "tfmm_plan_farfield", "tfmm_plan_destroy",
     "tfmm_aggregate", "tfmm_disaggregate", "tfmm_aggregate_dense", "tfmm_disaggregate_dense",
-    "tfmm_matvec_host", "tfmm_planewave", "tfmm_planewave_noalloc",
+    "tfmm_matvec_host", "tfmm_planewave", "tfmm_planewave_noalloc", "tfmm_plan_set_mrhs_precision",
 ]
 
 
@@ -44,7 +44,7 @@ class Params(ctypes.Structure):
         ("k", ctypes.c_double), ("box", ctypes.c_double), ("digits", ctypes.c_double),
         ("nphi_rule", ctypes.c_int32), ("L_override", ctypes.c_int32), ("tol", ctypes.c_double),
         ("quad_order", ctypes.c_int32), ("keep_dense", ctypes.c_int32), ("max_rhs", ctypes.c_int32),
-        ("batch_groups", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6),
+        ("batch_groups", ctypes.c_int32), ("mrhs_precision", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5),
     ]
 
 
@@ -54,7 +54,7 @@ class PlanInfo(ctypes.Structure):
         ("n_groups", ctypes.c_int32), ("K", ctypes.c_int32 * 3), ("n_rwg", ctypes.c_int64),
         ("max_n_beta", ctypes.c_int32), ("max_rank", ctypes.c_int32 * 3),
         ("tucker_bytes", ctypes.c_int64), ("tucker_bytes_alg", ctypes.c_int64), ("dense_bytes", ctypes.c_int64),
-        ("setup_ms", ctypes.c_double * 4),
+        ("setup_ms", ctypes.c_double * 4), ("kernel_errors", ctypes.c_int32), ("pad_", ctypes.c_int32),
     ]
 
     def as_dict(self):
@@ -63,7 +63,7 @@ class PlanInfo(ctypes.Structure):
             "n_groups": self.n_groups, "K": list(self.K), "n_rwg": self.n_rwg, "max_n_beta": self.max_n_beta,
             "max_rank": list(self.max_rank), "tucker_bytes": self.tucker_bytes,
             "tucker_bytes_alg": self.tucker_bytes_alg, "dense_bytes": self.dense_bytes,
-            "setup_ms": list(self.setup_ms),
+            "setup_ms": list(self.setup_ms), "kernel_errors": self.kernel_errors,
         }
 
 
@@ -104,6 +104,7 @@ def load():
         "tfmm_matvec_host": [P, P, P, I32, I32, P],
         "tfmm_planewave": [P, P, P, I32, P, P],
         "tfmm_planewave_noalloc": [P, P, P, I32, P, P],
+        "tfmm_plan_set_mrhs_precision": [P, I32],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -211,7 +212,8 @@ def tfmm_plan_create(mesh, params, stream=None):
     return Plan(h)
 
 
-def tfmm_plan_from_tucker(n_rwg, n_theta, n_phi, members, factors, weights=None, max_rhs=1, stream=None):
+def tfmm_plan_from_tucker(n_rwg, n_theta, n_phi, members, factors, weights=None, max_rhs=1, stream=None,
+                          mrhs_precision=0):
     """``members[g]``: global RWG ids of group g; ``factors[g][alpha] = (U_theta, U_phi, U_beta, core)``."""
     G = len(members)
     offsets = np.zeros(G + 1, np.int64)
@@ -231,7 +233,15 @@ def tfmm_plan_from_tucker(n_rwg, n_theta, n_phi, members, factors, weights=None,
     _check(load().tfmm_plan_from_tucker(n_rwg, G, n_theta, n_phi, _np_ptr(offsets), _np_ptr(ids), _np_ptr(ranks),
                                         _np_ptr(flat), None if w is None else _np_ptr(w), max_rhs, _stream(stream),
                                         ctypes.byref(h)))
-    return Plan(h)
+    plan = Plan(h)
+    if mrhs_precision:
+        tfmm_plan_set_mrhs_precision(plan, mrhs_precision)
+    return plan
+
+
+def tfmm_plan_set_mrhs_precision(plan, precision):
+    """0: FP32 CUDA-core chain for R > 1; 2 or 3: tensor cores with 2- or 3-term split BF16."""
+    _check(load().tfmm_plan_set_mrhs_precision(plan.handle, int(precision)))
 
 
 def tfmm_plan_set_dense(plan, tensors, stream=None):

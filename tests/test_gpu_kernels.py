@@ -239,3 +239,37 @@ def test_multi_rhs_chain_matches_oracle(name, R):
                 assert _rel(S[r, g, a], ref[g, a]) <= TOL, (r, g, a)
         refy = apply.disaggregate_all(T, members, g_in[r], n_rwg, w, beta=beta, y0=y0[r])
         assert _rel(Y[r], refy) <= TOL, r
+
+
+@pytest.mark.parametrize("terms,tol", [(3, 1e-5), (2, 5e-5)])
+@pytest.mark.parametrize("name,R", [("paper_like", 16), ("ragged", 7), ("odd_grid", 3)])
+def test_tensor_core_chain_matches_oracle(name, R, terms, tol):
+    """tcgen05 chains with FP32 operands split into `terms` BF16 terms, FP32 accumulation."""
+    tfmm = _tfmm()
+    nt, npf, nbetas, rank_fn = CASES[name]
+    n_rwg, members, T, factors = _case(700 + R, nt, npf, nbetas, rank_fn)
+    w = np.random.default_rng(19).uniform(0.05, 1.0, nt * npf)
+    plan = tfmm.tfmm_plan_from_tucker(n_rwg, nt, npf, members, factors, weights=w, max_rhs=R, mrhs_precision=terms)
+    G, nd = len(members), nt * npf
+    X = complex_gaussian((R, n_rwg), 800 + R)
+    xd = torch.from_numpy(X.astype(np.complex64)).cuda()
+    spec = torch.full((R, G, 2, nd), float("nan"), dtype=torch.complex64, device="cuda")
+    tfmm.tfmm_aggregate(plan, xd, spec)
+    g_in = complex_gaussian((R, G, 2, nd), 900 + R)
+    y0 = complex_gaussian((R, n_rwg), 1000 + R)
+    gd = torch.from_numpy(g_in.astype(np.complex64)).cuda()
+    yd = torch.from_numpy(y0.astype(np.complex64)).cuda()
+    beta = -0.5 + 0.125j
+    tfmm.tfmm_disaggregate(plan, gd, yd, beta=beta)
+    torch.cuda.synchronize()
+    assert plan.info["kernel_errors"] == 0
+    S = spec.cpu().numpy()
+    Y = yd.cpu().numpy()
+    assert np.isfinite(S).all() and np.isfinite(Y).all()
+    for r in range(R):
+        ref = apply.aggregate_all(T, members, X[r])
+        for g in range(G):
+            for a in range(2):
+                assert _rel(S[r, g, a], ref[g, a]) <= tol, (r, g, a, _rel(S[r, g, a], ref[g, a]))
+        refy = apply.disaggregate_all(T, members, g_in[r], n_rwg, w, beta=beta, y0=y0[r])
+        assert _rel(Y[r], refy) <= tol, (r, _rel(Y[r], refy))
