@@ -252,6 +252,70 @@ tfmm_status tfmm_planewave(const tfmm_plan* plan, const double* khat, const doub
 tfmm_status tfmm_planewave_noalloc(const tfmm_plan* plan, const double* khat, const double* pol, int32_t R,
                                    tfmm_cfloat* V, void* stream);
 
+/* ------------------------------------------------------------ runtime */
+
+/* Waits for the work queued on `stream` and reports kernel-side failures:
+ * TFMM_CUDA if a tensor-core tile gave up waiting on its own copies or MMAs
+ * since the plan was made (those outputs are then invalid).  No counterpart in
+ * the paper. */
+tfmm_status tfmm_sync(tfmm_plan* plan, void* stream);
+
+/* RWG -> (group, slot) table: for every RWG n < n_rwg (mesh order),
+ * group[n] is its box group (Sec. II.A) and slot[n] its position in that
+ * group's member list (tfmm_plan_members).  Host arrays of n_rwg int32. */
+tfmm_status tfmm_plan_rwg_perm(const tfmm_plan* plan, int32_t* group, int32_t* slot);
+
+/* Plan checkpoints.  tfmm_plan_save writes the grid, groups, geometry and the
+ * FP64 Tucker factors (Eq. 6) to `path`; tfmm_plan_load rebuilds a plan from
+ * such a file on the current device without repeating the setup (the dense
+ * tensors of keep_dense are not stored).  A file that is not a checkpoint of
+ * this build, is truncated, or holds inconsistent sizes, ranks, members or
+ * non-finite factors gives TFMM_IO.  The format is native little-endian. */
+tfmm_status tfmm_plan_save(const tfmm_plan* plan, const char* path);
+tfmm_status tfmm_plan_load(const char* path, void* stream, tfmm_plan** out);
+
+/* CUDA graphs of the hot path.  Captures stages (1 = aggregate x -> spectra,
+ * 2 = disaggregate spectra -> y, 3 = both, in that order) with the given
+ * device buffers and arguments (as tfmm_aggregate / tfmm_disaggregate), after
+ * running them once eagerly so that first-use allocations stay outside the
+ * graph; that eager pass writes the outputs (and applies beta to y).
+ * tfmm_graph_launch replays the graph on `stream`: the same buffers are read
+ * and written on every replay.  A graph must be destroyed before its plan
+ * (tfmm_plan_destroy refuses while graphs exist); replays follow the plan's
+ * one-stream ordering rule. */
+typedef struct tfmm_graph tfmm_graph;
+tfmm_status tfmm_graph_capture(tfmm_plan* plan, int32_t stages, const tfmm_cfloat* x, int32_t R, int64_t ldx,
+                               tfmm_cfloat* spectra, int32_t apply_weights, tfmm_cfloat beta, tfmm_cfloat* y,
+                               int64_t ldy, tfmm_graph** out);
+tfmm_status tfmm_graph_launch(tfmm_graph* graph, void* stream);
+tfmm_status tfmm_graph_destroy(tfmm_graph* graph);
+
+/* Tuning of the hot path.  Single RHS: threads per CTA (64..512, multiple of
+ * 32), CTAs per SM (0 = as many as fit) and the work-queue order (0 = most
+ * factor bytes first, 1 = group order) of the persistent aggregation and
+ * disaggregation kernels.  R > 1: the engine (mrhs_precision as in
+ * tfmm_params). */
+typedef struct {
+    int32_t agg_threads, agg_ctas_per_sm, agg_order;
+    int32_t dis_threads, dis_ctas_per_sm, dis_order;
+    int32_t agg_blocks, dis_blocks; /* resulting persistent grids (ignored by _set) */
+    int32_t mrhs_precision;
+    int32_t reserved[3];
+    double agg_ms, dis_ms;          /* times the autotuner measured (0 if not tuned) */
+} tfmm_tuning;
+tfmm_status tfmm_plan_tuning_get(const tfmm_plan* plan, tfmm_tuning* t);
+tfmm_status tfmm_plan_tuning_set(tfmm_plan* plan, const tfmm_tuning* t, void* stream);
+
+/* Autotuner: times candidate settings on the plan's own factors with scratch
+ * inputs (allocated and freed here; CUDA events on `stream`) and keeps the
+ * fastest.  R == 1 searches launch shape and queue order of each stage; R > 1
+ * chooses between the FP32 CUDA-core chain and the 3-term tensor-core chain
+ * (and the 2-term one when allow_two_term != 0, which is less accurate).
+ * The search stops early once budget_ms of wall time is spent.  `out` (may be
+ * NULL) receives the chosen tuning.  No counterpart in the paper. */
+tfmm_status tfmm_autotune(tfmm_plan* plan, int32_t R, double budget_ms, int32_t allow_two_term, void* stream,
+                          tfmm_tuning* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libtfmm.so")
 
-SOURCES = ["tfmm_host.cpp", "setup.cu", "apply.cu", "mrhs.cu", "mrhs_tc.cu"]
+SOURCES = ["tfmm_host.cpp", "runtime.cpp", "setup.cu", "apply.cu", "mrhs.cu", "mrhs_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off", "-Xptxas", "-v"]
 

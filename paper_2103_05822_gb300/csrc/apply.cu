@@ -488,7 +488,7 @@ SmemLayout dis_layout(const Plan& P, int NT) {
 }
 
 template <class K>
-Schedule make_schedule(K kernel, int NT, size_t smem, int num_sms, int n_items) {
+Schedule make_schedule(K kernel, int NT, size_t smem, int num_sms, int n_items, int ctas_per_sm = 0) {
     Schedule s;
     s.threads = NT;
     s.smem = smem;
@@ -497,6 +497,7 @@ Schedule make_schedule(K kernel, int NT, size_t smem, int num_sms, int n_items) 
     int per_sm = 0;
     TFMM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, NT, smem));
     if (per_sm < 1) fail(TFMM_INVALID_ARG, "work item too large for one CTA (shared memory " + std::to_string(smem) + " B)");
+    if (ctas_per_sm > 0) per_sm = std::min(per_sm, ctas_per_sm);
     s.blocks = std::max(1, std::min(per_sm * num_sms, n_items));
     return s;
 }
@@ -573,28 +574,43 @@ void pack_factors_fp32(Plan& P, cudaStream_t s) {
 void finalize_hot_layout(Plan& P, cudaStream_t s) {
     const int nI = P.G * 2;
     if (P.d_items) cudaFree(P.d_items);
-    if (P.d_agg_order) cudaFree(P.d_agg_order);
-    if (P.d_dis_order) cudaFree(P.d_dis_order);
-    P.d_items = nullptr; P.d_agg_order = nullptr; P.d_dis_order = nullptr;
+    P.d_items = nullptr;
     TFMM_CUDA_CHECK(cudaMalloc(&P.d_items, sizeof(TuckerItem) * nI));
     TFMM_CUDA_CHECK(cudaMemcpyAsync(P.d_items, P.items.data(), sizeof(TuckerItem) * nI, cudaMemcpyHostToDevice, s));
+    configure_hot(P, P.tuning, s);
+}
+
+// Queue orders (0: most factor bytes first, the LPT rule; 1: group order) and
+// persistent grids (threads per CTA, CTAs per SM capped by occupancy) of the
+// two single-RHS kernels.
+void configure_hot(Plan& P, const HotTuning& t, cudaStream_t s) {
+    const int nI = P.G * 2;
+    auto ok_threads = [](int nt) { return nt >= 64 && nt <= 512 && nt % 32 == 0; };
+    TFMM_REQUIRE(ok_threads(t.agg_threads) && ok_threads(t.dis_threads), "threads per CTA must be 64..512, a multiple of 32");
+    TFMM_REQUIRE(t.agg_ctas_per_sm >= 0 && t.dis_ctas_per_sm >= 0, "CTAs per SM must be >= 0");
+    TFMM_REQUIRE((t.agg_order == 0 || t.agg_order == 1) && (t.dis_order == 0 || t.dis_order == 1), "order must be 0 or 1");
     auto bytes = [&](const TuckerItem& d) {
         return (double)d.rb * d.ld_nb + (double)d.rb * d.ld_ab + (double)P.n_phi * d.rp + (double)P.n_theta * d.rt;
     };
     std::vector<int> agg(nI), dis(P.G);
     std::iota(agg.begin(), agg.end(), 0);
     std::iota(dis.begin(), dis.end(), 0);
-    std::stable_sort(agg.begin(), agg.end(), [&](int a, int b) { return bytes(P.items[a]) > bytes(P.items[b]); });
-    std::stable_sort(dis.begin(), dis.end(), [&](int a, int b) {
-        return bytes(P.items[2 * a]) + bytes(P.items[2 * a + 1]) > bytes(P.items[2 * b]) + bytes(P.items[2 * b + 1]);
-    });
-    TFMM_CUDA_CHECK(cudaMalloc(&P.d_agg_order, sizeof(int) * nI));
-    TFMM_CUDA_CHECK(cudaMalloc(&P.d_dis_order, sizeof(int) * std::max(P.G, 1)));
+    if (t.agg_order == 0)
+        std::stable_sort(agg.begin(), agg.end(), [&](int a, int b) { return bytes(P.items[a]) > bytes(P.items[b]); });
+    if (t.dis_order == 0)
+        std::stable_sort(dis.begin(), dis.end(), [&](int a, int b) {
+            return bytes(P.items[2 * a]) + bytes(P.items[2 * a + 1]) > bytes(P.items[2 * b]) + bytes(P.items[2 * b + 1]);
+        });
+    if (!P.d_agg_order) TFMM_CUDA_CHECK(cudaMalloc(&P.d_agg_order, sizeof(int) * nI));
+    if (!P.d_dis_order) TFMM_CUDA_CHECK(cudaMalloc(&P.d_dis_order, sizeof(int) * std::max(P.G, 1)));
+    // stream-ordered: launches already queued keep reading the old order until these copies land
     TFMM_CUDA_CHECK(cudaMemcpyAsync(P.d_agg_order, agg.data(), sizeof(int) * nI, cudaMemcpyHostToDevice, s));
     TFMM_CUDA_CHECK(cudaMemcpyAsync(P.d_dis_order, dis.data(), sizeof(int) * P.G, cudaMemcpyHostToDevice, s));
-    const int NT = 512;
-    P.agg_sched = make_schedule(tucker_aggregate_kernel, NT, sizeof(float2) * agg_layout(P, NT).total, P.num_sms, nI);
-    P.dis_sched = make_schedule(tucker_disaggregate_kernel, NT, sizeof(float2) * dis_layout(P, NT).total, P.num_sms, P.G);
+    P.agg_sched = make_schedule(tucker_aggregate_kernel, t.agg_threads,
+                                sizeof(float2) * agg_layout(P, t.agg_threads).total, P.num_sms, nI, t.agg_ctas_per_sm);
+    P.dis_sched = make_schedule(tucker_disaggregate_kernel, t.dis_threads,
+                                sizeof(float2) * dis_layout(P, t.dis_threads).total, P.num_sms, P.G, t.dis_ctas_per_sm);
+    P.tuning = t;
     TFMM_CUDA_CHECK(cudaStreamSynchronize(s));
 }
 

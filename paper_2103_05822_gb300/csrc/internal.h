@@ -135,13 +135,31 @@ struct TcStagePlan {
     int max_kt = 1, max_bn = 16;  // largest K-tile count and BN over the stage's problems
     ~TcStagePlan();
 };
+// Fused AG3 + AG4 (one launch): padded operand sizes shared by all its CTAs.
+struct FusedShape {
+    int K1 = 0, K2 = 0;      // r_phi and r_theta padded to 16 (the two contraction depths)
+    int N1p = 0, N1s = 0;    // largest r_theta x (RHS per CTA), padded to 16 (MMA N) and 32 (TMEM spacing)
+    int ntp = 0, nt32 = 0;   // n_theta padded to 16 (MMA N) and 32 (TMEM spacing)
+    int tcols = 0;           // TMEM columns per CTA
+    size_t smem = 0;         // dynamic shared memory per CTA
+};
+
 struct TcPlan {             // per (R, terms): problem lists of the 8 steps and scratch planes
     int R = 0, T = 0;
     TcStagePlan st[8];
-    std::vector<TcProb> host_probs[8];
-    void* last_out[8] = {};
     void* buf[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    // fused AG3 + AG4, when every item fits one CTA (else the two stages run apart)
+    bool fused34 = false;
+    FusedShape f34;
+    DeviceBuffer f34_items, f34_tiles;
+    int f34_ntiles = 0;
     ~TcPlan();
+};
+
+// Launch shape and queue order of the single-RHS kernels (set by the autotuner).
+struct HotTuning {
+    int agg_threads = 512, agg_ctas_per_sm = 0, agg_order = 0;  // ctas 0: as many as fit
+    int dis_threads = 512, dis_ctas_per_sm = 0, dis_order = 0;  // order 0: longest first, 1: group order
 };
 
 struct Schedule {
@@ -188,6 +206,9 @@ struct Plan {
     int* d_dis_order = nullptr;        // group ids, longest first
     std::vector<TuckerItem> items;
     Schedule agg_sched, dis_sched;
+    HotTuning tuning;
+    double tuned_ms[2] = {0, 0};       // autotuner's best aggregate / disaggregate times
+    int live_graphs = 0;               // captured graphs that still point into this plan
     int max_nb = 0, max_ldnb = 0, max_rank[3] = {0, 0, 0}, max_ldab = 0;
     // device: dense
     float2* d_dense = nullptr;
@@ -205,9 +226,8 @@ struct Plan {
     // multi-RHS chains, one per R used so far
     std::vector<std::unique_ptr<MrPlan>> mr;
     // tensor-core chains: factor planes (built on first use) and one chain per (R, terms)
-    int tc_terms = 0;
-    DeviceBuffer tc_fac;               // bf16 planes of every factor
-    std::vector<TcItem> tc_items;
+    DeviceBuffer tc_fac[4];            // [T]: bf16 planes of every factor, T = 2, 3 (kept: chains point here)
+    std::vector<TcItem> tc_items[4];
     DeviceBuffer tc_err;               // int: waits that gave up
     std::vector<std::unique_ptr<TcPlan>> tc;
     // workspace of tfmm_matvec_host
@@ -216,6 +236,28 @@ struct Plan {
 
     ~Plan();
 };
+
+// tfmm_host.cpp
+std::string& last_error();  // message of the calling thread's last failure
+void upload_common(Plan& P, cudaStream_t s);
+
+template <class F>
+tfmm_status guarded(F&& f) {
+    try {
+        last_error().clear();
+        f();
+        return TFMM_OK;
+    } catch (const Error& e) {
+        last_error() = e.what();
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        last_error() = "host allocation failed";
+        return TFMM_OOM;
+    } catch (const std::exception& e) {
+        last_error() = e.what();
+        return TFMM_INVALID_ARG;
+    }
+}
 
 // setup.cu
 void build_tucker_setup(Plan& P, const Mesh& M, cudaStream_t s);
@@ -234,6 +276,7 @@ void launch_dense_aggregate(const Plan& P, const float2* x, int R, int64_t ldx, 
 void launch_dense_disaggregate(const Plan& P, const float2* spec, int R, int weights, float2 beta, float2* y,
                                int64_t ldy, cudaStream_t s);
 void pack_factors_fp32(Plan& P, cudaStream_t s);  // from P.f64 into P.d_factors
+void configure_hot(Plan& P, const HotTuning& t, cudaStream_t s);  // orders and schedules of the 1-RHS kernels
 // mrhs_tc.cu
 void build_tc_factors(Plan& P, int T, cudaStream_t s);
 TcPlan* get_tc_plan(Plan& P, int R, int T, cudaStream_t s);
@@ -250,3 +293,10 @@ void pack_dense_fp32_from_f64(Plan& P, const double2* src, int g, int alpha, cud
 inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
 }  // namespace tfmm
+
+struct tfmm_mesh {
+    tfmm::Mesh m;
+};
+struct tfmm_plan {
+    tfmm::Plan p;
+};

@@ -37,6 +37,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstdlib>
+#include <numeric>
 #include <vector>
 
 #include "internal.h"
@@ -57,6 +58,8 @@ constexpr long kWaitLimit = 1L << 26;
 enum TcStage { TAG1, TAG2, TAG3, TAG4, TDG1A, TDG1B, TDG2, TDG3 };
 
 struct TcCtx {
+    float2* spec;        // AG4 output (spectra)
+    float2* y;           // DG3 output
     const int* grp_rwg;
     int64_t ld;          // ldy (DG3)
     float2 beta;         // DG3
@@ -181,7 +184,7 @@ __device__ __forceinline__ void epilogue(const TcCtx& c, const TcProb& p, int i,
         } break;
         case TAG4: {  // spectra; i = i_phi + n_phi r, j = i_theta
             const int ip = i % p.n_phi, r = i / p.n_phi;
-            float2* F = reinterpret_cast<float2*>(p.out);
+            float2* F = c.spec;
             F[(((int64_t)r * c.G + p.g) * 2 + p.alpha) * c.n_dir + j + (int64_t)c.n_theta * ip] = v;
         } break;
         case TDG1A: {  // P'' stored [a + r_t r][i_phi]; i = i_phi + n_phi r, j = a
@@ -196,8 +199,7 @@ __device__ __forceinline__ void epilogue(const TcCtx& c, const TcProb& p, int i,
             store_planes<T>(o, p.o_ps, (int64_t)j * p.o_ld + i, v);
             break;
         case TDG3: {  // y = beta y + conj(v); i = n, j = r
-            float2* y = reinterpret_cast<float2*>(p.out);
-            float2* dst = y + (int64_t)c.grp_rwg[p.rwg + i] + c.ld * j;
+            float2* dst = c.y + (int64_t)c.grp_rwg[p.rwg + i] + c.ld * j;
             float2 r = make_float2(v.x, -v.y);
             if (c.beta.x != 0.f || c.beta.y != 0.f) {
                 const float2 old = *dst;
@@ -338,6 +340,201 @@ __global__ void __launch_bounds__(TTHREADS) tc_gemm_kernel(const TcCtx c, const 
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(tcols));
 }
 
+// ------------------------------------------------------ fused AG3 + AG4
+// One CTA per (item, block of nr RHS).  AG3 runs as one GEMM with the phi
+// directions on the TMEM lanes, D1[i_phi][(a, r)] = sum_b U_phi[i_phi][b] M'_r[a][b]
+// (Fig. 2b step 2); then for each r of the block V_r = D1[:, (., r)] goes
+// TMEM -> registers -> shared memory (split into BF16 terms) as the A operand of
+// AG4, F_r[i_phi][i_theta] = sum_a V_r[i_phi][a] U_theta[i_theta][a] (Fig. 2b
+// steps 3-4), which leaves TMEM straight for the spectra.  The MMAs of r overlap
+// the spectra stores of r - 1 (two D2 accumulators).
+struct F34Item {
+    const bf16* uph; int64_t uph_ld, uph_ps;  // U_phi planes [i_phi][b]
+    const bf16* uth; int64_t uth_ld, uth_ps;  // U_theta planes [i_theta][a]
+    const bf16* m;   int64_t m_ld, m_ps;      // M' planes [a + r_t r][b]
+    int g, alpha, rt, rp;
+};
+struct F34Tile { int item, r0, nr; };
+
+__device__ __forceinline__ uint64_t make_desc_sbo(uint32_t addr, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)(128 >> 4) << 16;              // next core matrix along K
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;   // next 8-row group
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// 2T planes of `rows` rows (zero-filled from row `valid` and from column r8(kvalid))
+// of a K-major source into the canonical no-swizzle layout with depth K.
+template <int T>
+__device__ __forceinline__ void load_planes(uint8_t* dst, int plane_bytes, int K, const bf16* src, int64_t ld,
+                                            int64_t ps, int rows, int valid, int kvalid) {
+    const int kc8 = K / 8, k8v = (kvalid + 7) / 8;
+    const int total = 2 * T * rows * kc8;
+    for (int idx = threadIdx.x; idx < total; idx += TTHREADS) {
+        const int pl = idx / (rows * kc8), rem = idx % (rows * kc8), r = rem / kc8, kc = rem % kc8;
+        const bool ok = r < valid && kc < k8v;
+        const bf16* g = ok ? src + pl * ps + (int64_t)r * ld + kc * 8 : src;
+        cp16(dst + pl * plane_bytes + (r >> 3) * (K * 16) + kc * 128 + (r & 7) * 16, g, ok ? 16 : 0);
+    }
+}
+
+template <int T>
+__device__ __forceinline__ void issue_products(uint32_t d_re, uint32_t d_im, uint32_t a, int a_plane, uint32_t b,
+                                               int b_plane, uint32_t sbo_a, uint32_t sbo_b, int ksteps,
+                                               uint32_t idesc) {
+    constexpr int PI[6] = {0, 0, 1, 0, 1, 2}, PJ[6] = {0, 1, 0, 2, 1, 0};
+    const uint32_t idesc_neg = idesc | (1u << 13);
+    for (int ks = 0; ks < ksteps; ++ks)
+#pragma unroll
+        for (int q = 0; q < n_products<T>(); ++q) {
+            const uint32_t ar = a + PI[q] * a_plane + ks * 256, ai = a + (T + PI[q]) * a_plane + ks * 256;
+            const uint32_t br = b + PJ[q] * b_plane + ks * 256, bi = b + (T + PJ[q]) * b_plane + ks * 256;
+            const uint32_t acc = (ks > 0 || q > 0) ? 1u : 0u;
+            mma_bf16(d_re, make_desc_sbo(ar, sbo_a), make_desc_sbo(br, sbo_b), idesc, acc);
+            mma_bf16(d_re, make_desc_sbo(ai, sbo_a), make_desc_sbo(bi, sbo_b), idesc_neg, 1u);
+            mma_bf16(d_im, make_desc_sbo(ar, sbo_a), make_desc_sbo(bi, sbo_b), idesc, acc);
+            mma_bf16(d_im, make_desc_sbo(ai, sbo_a), make_desc_sbo(br, sbo_b), idesc, 1u);
+        }
+}
+
+__device__ __forceinline__ uint32_t idesc_bf16(int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(TBM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar)));
+}
+
+template <int T>
+__global__ void __launch_bounds__(TTHREADS) tc_ag34_kernel(const TcCtx c, const F34Item* __restrict__ items,
+                                                          const F34Tile* __restrict__ tiles, const FusedShape sh,
+                                                          int n_phi) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ __align__(8) uint64_t mbar[3];  // AG3 done, D2 buffer 0, D2 buffer 1
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const F34Tile t = tiles[blockIdx.x];
+    const F34Item it = items[t.item];
+    const int K1 = sh.K1, K2 = sh.K2, nt = c.n_theta;
+    const int a1p = TBM * K1 * 2, b1p = sh.N1p * K1 * 2, b2p = sh.ntp * K2 * 2, a2p = TBM * K2 * 2;
+    uint8_t* sA1 = smem;
+    uint8_t* sB1 = sA1 + 2 * T * a1p;
+    uint8_t* sB2 = sB1 + 2 * T * b1p;
+    uint8_t* sA2 = sB2 + 2 * T * b2p;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(sh.tcols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0)
+        for (int b = 0; b < 3; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[b])), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    const int n1 = it.rt * t.nr, n1p = (n1 + 15) & ~15;
+    load_planes<T>(sA1, a1p, K1, it.uph, it.uph_ld, it.uph_ps, n_phi, n_phi, it.rp);
+    load_planes<T>(sB1, b1p, K1, it.m + (int64_t)it.rt * t.r0 * it.m_ld, it.m_ld, it.m_ps, n1p, n1, it.rp);
+    load_planes<T>(sB2, b2p, K2, it.uth, it.uth_ld, it.uth_ps, sh.ntp, nt, it.rt);
+    asm volatile("cp.async.commit_group;");
+    asm volatile("cp.async.wait_group 0;");
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tm = tmem_base;
+    const uint32_t lanes = (uint32_t)(warp * 32) << 16;
+    const uint32_t d2 = tm + 2 * sh.N1s;  // D2 buffer b: re at d2 + 2 b nt32, im at + nt32
+    if (tid == 0)
+        issue_products<T>(tm, tm + sh.N1s, smem_u32(sA1), a1p, smem_u32(sB1), b1p, K1 * 16, K1 * 16, K1 / 16,
+                          idesc_bf16(n1p));
+    if (tid == 0) mma_commit(&mbar[0]);
+    bool ok = mbar_wait(&mbar[0], 0);
+    bool ag3_done = __syncthreads_and(ok);
+    ok = ag3_done;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const int phi = warp * 32 + lane;
+    const int64_t n_dir = c.n_dir;
+    int issued = -1;
+    for (int j = 0; j <= t.nr && ok; ++j) {
+        if (j > 0) {  // MMAs of j - 1 done: A2 is free and D2[(j-1)&1] holds F_{j-1}
+            const bool w = mbar_wait(&mbar[1 + ((j - 1) & 1)], ((j - 1) >> 1) & 1);
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            ok = __syncthreads_and(w);
+            if (!ok) break;
+        }
+        if (j < t.nr) {
+            // V_j: TMEM columns (a + r_t j) -> BF16 planes of A2, row i_phi, depth a (zeros past r_t)
+            for (int c0 = 0; c0 < K2; c0 += 32) {
+                uint32_t vr[32], vi[32];
+                tmem_ld32(vr, tm + lanes + it.rt * j + c0);
+                tmem_ld32(vi, tm + lanes + sh.N1s + it.rt * j + c0);
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+                for (int k8 = 0; k8 < 32; k8 += 8) {
+                    if (c0 + k8 >= K2) break;
+                    uint32_t w[2 * T][4];
+#pragma unroll
+                    for (int e = 0; e < 8; e += 2) {
+                        bf16 tr0[3], ti0[3], tr1[3], ti1[3];
+                        const int k = c0 + k8 + e;
+                        const float r0 = k < it.rt ? __uint_as_float(vr[k8 + e]) : 0.f;
+                        const float i0 = k < it.rt ? __uint_as_float(vi[k8 + e]) : 0.f;
+                        const float r1 = k + 1 < it.rt ? __uint_as_float(vr[k8 + e + 1]) : 0.f;
+                        const float i1 = k + 1 < it.rt ? __uint_as_float(vi[k8 + e + 1]) : 0.f;
+                        split_terms<T>(r0, tr0); split_terms<T>(i0, ti0);
+                        split_terms<T>(r1, tr1); split_terms<T>(i1, ti1);
+#pragma unroll
+                        for (int q = 0; q < T; ++q) {
+                            w[q][e / 2] = (uint32_t)__bfloat16_as_ushort(tr0[q]) |
+                                          ((uint32_t)__bfloat16_as_ushort(tr1[q]) << 16);
+                            w[T + q][e / 2] = (uint32_t)__bfloat16_as_ushort(ti0[q]) |
+                                              ((uint32_t)__bfloat16_as_ushort(ti1[q]) << 16);
+                        }
+                    }
+                    const int off = (phi >> 3) * (K2 * 16) + ((c0 + k8) >> 3) * 128 + (phi & 7) * 16;
+#pragma unroll
+                    for (int q = 0; q < 2 * T; ++q)
+                        *reinterpret_cast<uint4*>(sA2 + q * a2p + off) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;");
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t dr = d2 + 2 * (j & 1) * sh.nt32;
+                issue_products<T>(dr, dr + sh.nt32, smem_u32(sA2), a2p, smem_u32(sB2), b2p, K2 * 16, K2 * 16, K2 / 16,
+                                  idesc_bf16(sh.ntp));
+                mma_commit(&mbar[1 + (j & 1)]);
+            }
+            issued = j;
+        }
+        if (j > 0) {  // spectra of RHS r0 + j - 1, straight from TMEM
+            const uint32_t dr = d2 + 2 * ((j - 1) & 1) * sh.nt32;
+            const int r = t.r0 + j - 1;
+            float2* F = c.spec + (((int64_t)r * c.G + it.g) * 2 + it.alpha) * n_dir + (int64_t)nt * phi;
+            for (int c0 = 0; c0 < sh.ntp; c0 += 32) {
+                uint32_t vr[32], vi[32];
+                tmem_ld32(vr, dr + lanes + c0);
+                tmem_ld32(vi, dr + lanes + sh.nt32 + c0);
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+                if (phi < n_phi) {
+#pragma unroll 8
+                    for (int e = 0; e < 32; ++e)
+                        if (c0 + e < nt) F[c0 + e] = make_float2(__uint_as_float(vr[e]), __uint_as_float(vi[e]));
+                }
+            }
+        }
+    }
+    // no MMA may still run when TMEM is freed
+    if (!ag3_done) mbar_wait(&mbar[0], 0);
+    else if (issued >= 0 && !ok) mbar_wait(&mbar[1 + (issued & 1)], (issued >> 1) & 1);
+    if (!ok && tid == 0) atomicAdd(c.err, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(sh.tcols));
+}
+
 // ------------------------------------------------------------ operand prep
 // Split planes of an FP32 complex matrix: dst[p][r][k] for r < rows, k < cols,
 // src element (r, k) at src[r * sr + k * sk]; entries k in [cols, ld) stay as they are.
@@ -442,12 +639,10 @@ TcPlan::~TcPlan() {
 
 // BF16 planes of every factor in the two K-major layouts the chains read.
 void build_tc_factors(Plan& P, int T, cudaStream_t s) {
-    if (P.tc_terms == T && P.tc_fac.p) return;
-    if (P.tc_fac.p) cudaFree(P.tc_fac.p);
-    P.tc_fac.p = nullptr;
-    P.tc_terms = T;
+    if (P.tc_fac[T].p) return;
+    std::vector<TcItem>& items = P.tc_items[T];
     const int nt = P.n_theta, np = P.n_phi;
-    P.tc_items.assign(P.items.size(), TcItem{});
+    items.assign(P.items.size(), TcItem{});
     int64_t off = 0;
     auto add = [&](TcMat& m, int rows, int cols) {
         m.rows = rows;
@@ -458,7 +653,7 @@ void build_tc_factors(Plan& P, int T, cudaStream_t s) {
     };
     for (size_t q = 0; q < P.items.size(); ++q) {
         const TuckerItem& d = P.items[q];
-        TcItem& t = P.tc_items[q];
+        TcItem& t = items[q];
         const int m = d.rt * d.rp;
         add(t.ubT, d.rb, d.n_beta);   // [c][n]
         add(t.ub, d.n_beta, d.rb);    // [n][c]
@@ -469,9 +664,9 @@ void build_tc_factors(Plan& P, int T, cudaStream_t s) {
         add(t.uthT, nt, d.rt);        // [i_theta][a]
         add(t.uth, d.rt, nt);         // [a][i_theta]
     }
-    TFMM_CUDA_CHECK(cudaMalloc(&P.tc_fac.p, sizeof(bf16) * std::max<int64_t>(off, 1)));
-    TFMM_CUDA_CHECK(cudaMemsetAsync(P.tc_fac.p, 0, sizeof(bf16) * std::max<int64_t>(off, 1), s));
-    bf16* base = reinterpret_cast<bf16*>(P.tc_fac.p);
+    TFMM_CUDA_CHECK(cudaMalloc(&P.tc_fac[T].p, sizeof(bf16) * std::max<int64_t>(off, 1)));
+    TFMM_CUDA_CHECK(cudaMemsetAsync(P.tc_fac[T].p, 0, sizeof(bf16) * std::max<int64_t>(off, 1), s));
+    bf16* base = reinterpret_cast<bf16*>(P.tc_fac[T].p);
     auto conv = [&](const float2* src, int rows, int cols, int64_t sr, int64_t sk, const TcMat& m) {
         const int64_t ps = (int64_t)m.rows * m.ld;
         if (T == 2)
@@ -481,7 +676,7 @@ void build_tc_factors(Plan& P, int T, cudaStream_t s) {
     };
     for (size_t q = 0; q < P.items.size(); ++q) {
         const TuckerItem& d = P.items[q];
-        const TcItem& t = P.tc_items[q];
+        const TcItem& t = items[q];
         const int m = d.rt * d.rp;
         const float2* ub = P.d_factors + d.ub;      // U_beta^T rows: (c, n) at c ld_nb + n
         const float2* cc = P.d_factors + d.core;    // C_(3) rows:    (c, ab) at c ld_ab + ab
@@ -529,6 +724,92 @@ void upload_tc_stage(TcStagePlan& st, const std::vector<TcProb>& probs, const st
     TFMM_CUDA_CHECK(cudaMemcpy(st.d_tiles, tiles.data(), sizeof(MrTile) * tiles.size(), cudaMemcpyHostToDevice));
 }
 
+bool fused_enabled() {
+    static const bool on = [] {
+        const char* e = std::getenv("TFMM_TC_FUSED");
+        return e && e[0] == '1';
+    }();
+    return on;
+}
+
+constexpr size_t kMaxDynSmem = 225 * 1024;
+
+size_t f34_smem(int T, int K1, int K2, int N1p, int ntp) {
+    return (size_t)2 * T * 2 * ((size_t)TBM * K1 + (size_t)N1p * K1 + (size_t)ntp * K2 + (size_t)TBM * K2);
+}
+
+// Shapes and work list of the fused AG3 + AG4 kernel; leaves M.fused34 false
+// when some item cannot run in one CTA (n_phi > 128 lanes, TMEM or shared memory).
+template <class MOff>
+void plan_fused34(const Plan& P, TcPlan& M, const bf16* F, const std::vector<TcItem>& tci, const bf16* Mb, MOff moff) {
+    M.fused34 = false;
+    if (!fused_enabled()) return;
+    const int T = M.T, R = M.R, nt = P.n_theta, np = P.n_phi;
+    if (np > TBM || nt > 256) return;
+    FusedShape f;
+    f.K1 = (P.max_rank[1] + 15) & ~15;
+    f.K2 = (P.max_rank[0] + 15) & ~15;
+    f.ntp = (nt + 15) & ~15;
+    f.nt32 = (nt + 31) & ~31;
+    const int n1s_cap = ((512 - 4 * f.nt32) / 2) & ~31;
+    int n1max = std::min(256, n1s_cap);
+    while (n1max >= 16 && f34_smem(T, f.K1, f.K2, n1max, f.ntp) > kMaxDynSmem) n1max -= 16;
+    if (n1max < ((P.max_rank[0] + 15) & ~15)) return;
+    std::vector<F34Item> items(P.items.size());
+    std::vector<int> nr_of(P.items.size());
+    int n1p_max = 16;
+    for (size_t q = 0; q < P.items.size(); ++q) {
+        const TuckerItem& d = P.items[q];
+        const TcItem& ti = tci[q];
+        F34Item& it = items[q];
+        it.uph = F + ti.uphT.off; it.uph_ld = ti.uphT.ld; it.uph_ps = (int64_t)ti.uphT.rows * ti.uphT.ld;
+        it.uth = F + ti.uthT.off; it.uth_ld = ti.uthT.ld; it.uth_ps = (int64_t)ti.uthT.rows * ti.uthT.ld;
+        it.m = Mb + moff((int)q); it.m_ld = r8(d.rp); it.m_ps = (int64_t)d.rt * R * r8(d.rp);
+        it.g = d.g; it.alpha = d.alpha; it.rt = d.rt; it.rp = d.rp;
+        const int nr = std::max(1, std::min(R, n1max / d.rt));
+        nr_of[q] = nr;
+        n1p_max = std::max(n1p_max, (d.rt * nr + 15) & ~15);
+    }
+    f.N1p = n1p_max;
+    f.N1s = (n1p_max + 31) & ~31;
+    f.tcols = 32;
+    while (f.tcols < 2 * f.N1s + 4 * f.nt32) f.tcols *= 2;
+    if (f.tcols > 512) return;
+    f.smem = f34_smem(T, f.K1, f.K2, f.N1p, f.ntp);
+    // no more CTAs per SM than their TMEM allocations allow
+    constexpr size_t kSmemSM = 228 * 1024;
+    const int ctas_tmem = 512 / f.tcols;
+    if (kSmemSM / (f.smem + 2048) > (size_t)ctas_tmem) f.smem = std::min(kMaxDynSmem, kSmemSM / ctas_tmem - 2048);
+    // work list, most work first
+    std::vector<int> order(P.items.size());
+    std::iota(order.begin(), order.end(), 0);
+    auto cost = [&](int q) { return (double)P.items[q].rt * (P.items[q].rp + nt); };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    std::vector<F34Tile> tiles;
+    for (int q : order)
+        for (int r0 = 0; r0 < R; r0 += nr_of[q]) tiles.push_back(F34Tile{q, r0, std::min(nr_of[q], R - r0)});
+    TFMM_CUDA_CHECK(cudaMalloc(&M.f34_items.p, sizeof(F34Item) * items.size()));
+    TFMM_CUDA_CHECK(cudaMalloc(&M.f34_tiles.p, sizeof(F34Tile) * tiles.size()));
+    TFMM_CUDA_CHECK(cudaMemcpy(M.f34_items.p, items.data(), sizeof(F34Item) * items.size(), cudaMemcpyHostToDevice));
+    TFMM_CUDA_CHECK(cudaMemcpy(M.f34_tiles.p, tiles.data(), sizeof(F34Tile) * tiles.size(), cudaMemcpyHostToDevice));
+    M.f34_ntiles = (int)tiles.size();
+    M.f34 = f;
+    M.fused34 = true;
+}
+
+template <int T>
+void launch_ag34(const Plan& P, const TcPlan& M, const TcCtx& c, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        TFMM_CUDA_CHECK(cudaFuncSetAttribute(tc_ag34_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kMaxDynSmem));
+        attr = true;
+    }
+    tc_ag34_kernel<T><<<M.f34_ntiles, TTHREADS, M.f34.smem, s>>>(
+        c, static_cast<const F34Item*>(M.f34_items.p), static_cast<const F34Tile*>(M.f34_tiles.p), M.f34, P.n_phi);
+    TFMM_CUDA_CHECK(cudaGetLastError());
+}
+
 }  // namespace
 
 TcPlan* get_tc_plan(Plan& P, int R, int T, cudaStream_t s) {
@@ -541,7 +822,8 @@ TcPlan* get_tc_plan(Plan& P, int R, int T, cudaStream_t s) {
     M.T = T;
     const int nt = P.n_theta, np = P.n_phi;
     const int nI = P.G * 2;
-    const bf16* F = reinterpret_cast<const bf16*>(P.tc_fac.p);
+    const bf16* F = reinterpret_cast<const bf16*>(P.tc_fac[T].p);
+    const std::vector<TcItem>& tci = P.tc_items[T];
     // scratch planes: X (per group), T/S, M'/H, V''/P'', G' (per item)
     enum { BX, BT, BM, BV, BG, NB };
     int64_t sz[NB] = {0, 0, 0, 0, 0};
@@ -577,7 +859,7 @@ TcPlan* get_tc_plan(Plan& P, int R, int T, cudaStream_t s) {
     std::vector<MrTile> tl[8];
     for (int q = 0; q < nI; ++q) {
         const TuckerItem& d = P.items[q];
-        const TcItem& f = P.tc_items[q];
+        const TcItem& f = tci[q];
         const Off& o = of[q];
         const int m = d.rt * d.rp;
         TcProb b{};
@@ -640,8 +922,8 @@ TcPlan* get_tc_plan(Plan& P, int R, int T, cudaStream_t s) {
         TcProb p{};
         p.g = g; p.rwg = d0.rwg;
         p.M = d0.n_beta; p.N = R; p.K0 = d0.rb; p.K1 = d1.rb; p.BN = bn_of(R);
-        const TcMat& u0 = P.tc_items[2 * g].ub;
-        const TcMat& u1 = P.tc_items[2 * g + 1].ub;
+        const TcMat& u0 = tci[2 * g].ub;
+        const TcMat& u1 = tci[2 * g + 1].ub;
         p.A0 = F + u0.off; p.a_ld0 = u0.ld; p.a_ps0 = (int64_t)u0.rows * u0.ld;
         p.A1 = F + u1.off; p.a_ld1 = u1.ld; p.a_ps1 = (int64_t)u1.rows * u1.ld;
         p.B0 = Tb + of[2 * g].t; p.b_ld0 = of[2 * g].ldt; p.b_ps0 = (int64_t)R * of[2 * g].ldt;
@@ -649,39 +931,32 @@ TcPlan* get_tc_plan(Plan& P, int R, int T, cudaStream_t s) {
         add_tc_tiles(tl[TDG3], (int)pr[TDG3].size(), p.M, p.N); pr[TDG3].push_back(p);
     }
     for (int st = 0; st < 8; ++st) {
-        M.host_probs[st] = pr[st];
         upload_tc_stage(M.st[st], pr[st], tl[st]);
     }
+    plan_fused34(P, M, F, tci, Mb, [&](int q) { return of[q].m; });
     P.tc.push_back(std::move(tp));
     return P.tc.back().get();
 }
 
 namespace {
 
-// Output pointers that change per call (spectra, y) are patched into the problem lists.
-// (stream-ordered: earlier launches on the stream still read the old list)
-void set_outputs(TcPlan& M, int stage, void* out, cudaStream_t s) {
-    if (M.last_out[stage] == out) return;
-    std::vector<TcProb>& v = M.host_probs[stage];
-    for (auto& p : v) p.out = out;
-    TFMM_CUDA_CHECK(cudaMemcpyAsync(M.st[stage].d_probs, v.data(), sizeof(TcProb) * v.size(), cudaMemcpyHostToDevice, s));
-    TFMM_CUDA_CHECK(cudaStreamSynchronize(s));  // the host list may change again on the next call
-    M.last_out[stage] = out;
-}
-
 template <int T>
 void tc_aggregate_t(Plan& P, TcPlan& M, const float2* x, int R, int64_t ldx, float2* spec, cudaStream_t s) {
     TcCtx c{};
     c.grp_rwg = P.d_grp_rwg; c.R = R; c.G = P.G; c.n_theta = P.n_theta; c.n_dir = P.n_dir; c.err = static_cast<int*>(P.tc_err.p);
-    set_outputs(M, TAG4, spec, s);
+    c.spec = spec;
     dim3 gx(64, std::min(P.G * 2, 4096));
     prep_x_kernel<T><<<gx, 256, 0, s>>>(x, ldx, P.d_grp_rwg, reinterpret_cast<const TcProb*>(M.st[TAG1].d_probs),
                                         M.st[TAG1].n_probs, R);
     TFMM_CUDA_CHECK(cudaGetLastError());
     launch_tc<T, TAG1>(M.st[TAG1], c, s);
     launch_tc<T, TAG2>(M.st[TAG2], c, s);
-    launch_tc<T, TAG3>(M.st[TAG3], c, s);
-    launch_tc<T, TAG4>(M.st[TAG4], c, s);
+    if (M.fused34) {
+        launch_ag34<T>(P, M, c, s);
+    } else {
+        launch_tc<T, TAG3>(M.st[TAG3], c, s);
+        launch_tc<T, TAG4>(M.st[TAG4], c, s);
+    }
 }
 
 template <int T>
@@ -690,7 +965,7 @@ void tc_disaggregate_t(Plan& P, TcPlan& M, const float2* spec, int R, int weight
     TcCtx c{};
     c.grp_rwg = P.d_grp_rwg; c.R = R; c.G = P.G; c.n_theta = P.n_theta; c.n_dir = P.n_dir; c.err = static_cast<int*>(P.tc_err.p);
     c.ld = ldy; c.beta = beta;
-    set_outputs(M, TDG3, y, s);
+    c.y = y;
     dim3 gg(64, std::min(P.G * 2, 4096));
     prep_g_kernel<T><<<gg, 256, 0, s>>>(spec, weights ? P.d_weights : nullptr,
                                         reinterpret_cast<const TcProb*>(M.st[TDG1A].d_probs), M.st[TDG1A].n_probs, R,

@@ -12,35 +12,28 @@
 
 #include "internal.h"
 
-struct tfmm_mesh {
-    tfmm::Mesh m;
-};
-struct tfmm_plan {
-    tfmm::Plan p;
-};
-
 namespace tfmm {
-namespace {
 
-thread_local std::string g_last_error;
-
-template <class F>
-tfmm_status guarded(F&& f) {
-    try {
-        g_last_error.clear();
-        f();
-        return TFMM_OK;
-    } catch (const Error& e) {
-        g_last_error = e.what();
-        return e.code;
-    } catch (const std::bad_alloc&) {
-        g_last_error = "host allocation failed";
-        return TFMM_OOM;
-    } catch (const std::exception& e) {
-        g_last_error = e.what();
-        return TFMM_INVALID_ARG;
-    }
+std::string& last_error() {
+    thread_local std::string msg;
+    return msg;
 }
+
+void upload_common(Plan& P, cudaStream_t s) {
+    int dev = 0;
+    TFMM_CUDA_CHECK(cudaGetDevice(&dev));
+    TFMM_CUDA_CHECK(cudaDeviceGetAttribute(&P.num_sms, cudaDevAttrMultiProcessorCount, dev));
+    std::vector<int> ids(P.grp_rwg.begin(), P.grp_rwg.end());
+    TFMM_CUDA_CHECK(cudaMalloc(&P.d_grp_rwg, sizeof(int) * std::max<int64_t>(P.N, 1)));
+    TFMM_CUDA_CHECK(cudaMemcpyAsync(P.d_grp_rwg, ids.data(), sizeof(int) * P.N, cudaMemcpyHostToDevice, s));
+    TFMM_CUDA_CHECK(cudaMalloc(&P.d_weights, sizeof(float) * P.n_dir));
+    TFMM_CUDA_CHECK(cudaMemcpyAsync(P.d_weights, P.weights.data(), sizeof(float) * P.n_dir, cudaMemcpyHostToDevice, s));
+    TFMM_CUDA_CHECK(cudaMalloc(&P.d_counters, sizeof(unsigned) * 16));
+    TFMM_CUDA_CHECK(cudaMemsetAsync(P.d_counters, 0, sizeof(unsigned) * 16, s));
+    TFMM_CUDA_CHECK(cudaStreamSynchronize(s));
+}
+
+namespace {
 
 // RWG functions (Sec. II.A, ref. [20]): every edge shared by exactly two
 // triangles; RWGs sorted by (min, max) vertex id; T+ the lower triangle id.
@@ -151,19 +144,6 @@ void make_groups(Plan& P, const Mesh& M, double box) {
     P.N = N;
 }
 
-void upload_common(Plan& P, cudaStream_t s) {
-    int dev = 0;
-    TFMM_CUDA_CHECK(cudaGetDevice(&dev));
-    TFMM_CUDA_CHECK(cudaDeviceGetAttribute(&P.num_sms, cudaDevAttrMultiProcessorCount, dev));
-    std::vector<int> ids(P.grp_rwg.begin(), P.grp_rwg.end());
-    TFMM_CUDA_CHECK(cudaMalloc(&P.d_grp_rwg, sizeof(int) * std::max<int64_t>(P.N, 1)));
-    TFMM_CUDA_CHECK(cudaMemcpyAsync(P.d_grp_rwg, ids.data(), sizeof(int) * P.N, cudaMemcpyHostToDevice, s));
-    TFMM_CUDA_CHECK(cudaMalloc(&P.d_weights, sizeof(float) * P.n_dir));
-    TFMM_CUDA_CHECK(cudaMemcpyAsync(P.d_weights, P.weights.data(), sizeof(float) * P.n_dir, cudaMemcpyHostToDevice, s));
-    TFMM_CUDA_CHECK(cudaMalloc(&P.d_counters, sizeof(unsigned) * 16));
-    TFMM_CUDA_CHECK(cudaMemsetAsync(P.d_counters, 0, sizeof(unsigned) * 16, s));
-    TFMM_CUDA_CHECK(cudaStreamSynchronize(s));
-}
 
 void check_params(const tfmm_params& p) {
     TFMM_REQUIRE(std::isfinite(p.k) && p.k > 0, "k must be positive");
@@ -207,7 +187,7 @@ using namespace tfmm;
 
 extern "C" {
 
-const char* tfmm_last_error(void) { return g_last_error.c_str(); }
+const char* tfmm_last_error(void) { return last_error().c_str(); }
 
 tfmm_status tfmm_params_default(tfmm_params* p) {
     return guarded([&] {
@@ -515,7 +495,10 @@ tfmm_status tfmm_plan_farfield(const tfmm_plan* plan, int32_t g, tfmm_cdouble* A
 }
 
 tfmm_status tfmm_plan_destroy(tfmm_plan* plan) {
-    return guarded([&] { delete plan; });
+    return guarded([&] {
+        if (plan) TFMM_REQUIRE(plan->p.live_graphs == 0, "destroy the plan's graphs first");
+        delete plan;
+    });
 }
 
 tfmm_status tfmm_aggregate(tfmm_plan* plan, const tfmm_cfloat* x, int32_t R, int64_t ldx, tfmm_cfloat* spectra,

@@ -26,6 +26,9 @@ EXPORTED = [
     "tfmm_plan_export_factors", "tfmm_plan_farfield", "tfmm_plan_destroy",
     "tfmm_aggregate", "tfmm_disaggregate", "tfmm_aggregate_dense", "tfmm_disaggregate_dense",
     "tfmm_matvec_host", "tfmm_planewave", "tfmm_planewave_noalloc", "tfmm_plan_set_mrhs_precision",
+    "tfmm_sync", "tfmm_plan_rwg_perm", "tfmm_plan_save", "tfmm_plan_load",
+    "tfmm_graph_capture", "tfmm_graph_launch", "tfmm_graph_destroy",
+    "tfmm_plan_tuning_get", "tfmm_plan_tuning_set", "tfmm_autotune",
 ]
 
 
@@ -67,6 +70,20 @@ class PlanInfo(ctypes.Structure):
         }
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [
+        ("agg_threads", ctypes.c_int32), ("agg_ctas_per_sm", ctypes.c_int32), ("agg_order", ctypes.c_int32),
+        ("dis_threads", ctypes.c_int32), ("dis_ctas_per_sm", ctypes.c_int32), ("dis_order", ctypes.c_int32),
+        ("agg_blocks", ctypes.c_int32), ("dis_blocks", ctypes.c_int32), ("mrhs_precision", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3), ("agg_ms", ctypes.c_double), ("dis_ms", ctypes.c_double),
+    ]
+    _names = ("agg_threads", "agg_ctas_per_sm", "agg_order", "dis_threads", "dis_ctas_per_sm", "dis_order",
+              "agg_blocks", "dis_blocks", "mrhs_precision", "agg_ms", "dis_ms")
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k in self._names}
+
+
 def library_path():
     return _LIB_PATH
 
@@ -105,6 +122,16 @@ def load():
         "tfmm_planewave": [P, P, P, I32, P, P],
         "tfmm_planewave_noalloc": [P, P, P, I32, P, P],
         "tfmm_plan_set_mrhs_precision": [P, I32],
+        "tfmm_sync": [P, P],
+        "tfmm_plan_rwg_perm": [P, P, P],
+        "tfmm_plan_save": [P, ctypes.c_char_p],
+        "tfmm_plan_load": [ctypes.c_char_p, P, P],
+        "tfmm_graph_capture": [P, I32, P, I32, I64, P, I32, cfloat, P, I64, P],
+        "tfmm_graph_launch": [P, P],
+        "tfmm_graph_destroy": [P],
+        "tfmm_plan_tuning_get": [P, P],
+        "tfmm_plan_tuning_set": [P, P, P],
+        "tfmm_autotune": [P, I32, D, I32, P, P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -368,3 +395,90 @@ def tfmm_planewave_noalloc(plan, khat, pol, V, stream=None):
     p = np.ascontiguousarray(pol, np.float64).reshape(-1, 3)
     _check(load().tfmm_planewave_noalloc(plan.handle, _np_ptr(k), _np_ptr(p), k.shape[0], _dev_ptr(V),
                                          _stream(stream)))
+
+
+# ------------------------------------------------------------------- runtime
+def tfmm_sync(plan, stream=None):
+    """Waits for `stream`; raises if a tensor-core tile gave up waiting."""
+    _check(load().tfmm_sync(plan.handle, _stream(stream)))
+
+
+def tfmm_plan_rwg_perm(plan):
+    """(group, slot) int32 arrays over the RWGs in mesh order."""
+    n = plan.info["n_rwg"]
+    grp = np.empty(n, np.int32)
+    slot = np.empty(n, np.int32)
+    _check(load().tfmm_plan_rwg_perm(plan.handle, _np_ptr(grp), _np_ptr(slot)))
+    return grp, slot
+
+
+def tfmm_plan_save(plan, path):
+    _check(load().tfmm_plan_save(plan.handle, os.fsencode(path)))
+
+
+def tfmm_plan_load(path, stream=None):
+    h = ctypes.c_void_p()
+    _check(load().tfmm_plan_load(os.fsencode(path), _stream(stream), ctypes.byref(h)))
+    return Plan(h)
+
+
+class Graph:
+    """A captured aggregate / disaggregate (tfmm_graph); keeps its plan and buffers alive."""
+
+    def __init__(self, handle, plan, buffers):
+        self.handle = handle
+        self.plan = plan
+        self.buffers = buffers
+
+    def launch(self, stream=None):
+        _check(load().tfmm_graph_launch(self.handle, _stream(stream)))
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.tfmm_graph_destroy(self.handle)
+            self.handle = None
+
+
+def tfmm_graph_capture(plan, stages, spectra, x=None, y=None, R=None, apply_weights=True, beta=0.0):
+    """stages: 1 aggregate x -> spectra, 2 disaggregate spectra -> y, 3 both (runs them once eagerly)."""
+    if R is None:
+        R = spectra.shape[0]
+    ldx = 0 if x is None else (x.shape[0] if x.dim() == 1 else x.stride(0))
+    ldy = 0 if y is None else (y.shape[0] if y.dim() == 1 else y.stride(0))
+    b = cfloat(float(np.real(beta)), float(np.imag(beta)))
+    h = ctypes.c_void_p()
+    _check(load().tfmm_graph_capture(plan.handle, int(stages), None if x is None else _dev_ptr(x), R, ldx,
+                                     _dev_ptr(spectra), int(bool(apply_weights)), b,
+                                     None if y is None else _dev_ptr(y), ldy, ctypes.byref(h)))
+    return Graph(h, plan, (x, spectra, y))
+
+
+def tfmm_graph_launch(graph, stream=None):
+    graph.launch(stream)
+
+
+def tfmm_graph_destroy(graph):
+    if graph.handle:
+        _check(load().tfmm_graph_destroy(graph.handle))
+        graph.handle = None
+
+
+def tfmm_plan_tuning_get(plan):
+    t = Tuning()
+    _check(load().tfmm_plan_tuning_get(plan.handle, ctypes.byref(t)))
+    return t.as_dict()
+
+
+def tfmm_plan_tuning_set(plan, stream=None, **fields):
+    t = Tuning()
+    _check(load().tfmm_plan_tuning_get(plan.handle, ctypes.byref(t)))
+    for k, v in fields.items():
+        setattr(t, k, v)
+    _check(load().tfmm_plan_tuning_set(plan.handle, ctypes.byref(t), _stream(stream)))
+
+
+def tfmm_autotune(plan, R=1, budget_ms=2000.0, allow_two_term=False, stream=None):
+    t = Tuning()
+    _check(load().tfmm_autotune(plan.handle, int(R), float(budget_ms), int(bool(allow_two_term)), _stream(stream),
+                                ctypes.byref(t)))
+    return t.as_dict()

@@ -103,3 +103,35 @@ def test_plan_params_validated_before_any_gpu_work(lib):
         with pytest.raises(tfmm.TfmmError) as e:
             tfmm.tfmm_plan_create(mesh, p, stream=0)
         assert e.value.status == tfmm.INVALID_ARG
+
+
+def test_runtime_calls_reject_null_arguments(lib):
+    out = ctypes.c_void_p()
+    z = tfmm.cfloat(0.0, 0.0)
+    assert lib.tfmm_sync(None, None) == tfmm.INVALID_ARG
+    assert lib.tfmm_plan_rwg_perm(None, None, None) == tfmm.INVALID_ARG
+    assert lib.tfmm_plan_save(None, b"/nonexistent/x") == tfmm.INVALID_ARG
+    assert lib.tfmm_plan_load(None, None, ctypes.byref(out)) == tfmm.INVALID_ARG
+    assert lib.tfmm_graph_capture(None, 1, None, 1, 1, None, 1, z, None, 1, ctypes.byref(out)) == tfmm.INVALID_ARG
+    assert lib.tfmm_graph_launch(None, None) == tfmm.INVALID_ARG
+    assert lib.tfmm_graph_destroy(None) == tfmm.OK
+    assert lib.tfmm_plan_tuning_get(None, None) == tfmm.INVALID_ARG
+    assert lib.tfmm_plan_tuning_set(None, None, None) == tfmm.INVALID_ARG
+    assert lib.tfmm_autotune(None, 1, 10.0, 0, None, None) == tfmm.INVALID_ARG
+
+
+def test_checkpoint_load_rejects_missing_and_foreign_files(lib, tmp_path):
+    """Header checks run before any device work, so they are testable here."""
+    with pytest.raises(tfmm.TfmmError) as e:
+        tfmm.tfmm_plan_load(str(tmp_path / "missing.tfmm"), stream=0)
+    assert e.value.status == tfmm.IO
+    junk = tmp_path / "junk.tfmm"
+    junk.write_bytes(b"NOTAPLAN" + bytes(64))
+    with pytest.raises(tfmm.TfmmError) as e:
+        tfmm.tfmm_plan_load(str(junk), stream=0)
+    assert e.value.status == tfmm.IO
+    short = tmp_path / "short.tfmm"
+    short.write_bytes(b"TFMMPLAN\x01\x00")
+    with pytest.raises(tfmm.TfmmError) as e:
+        tfmm.tfmm_plan_load(str(short), stream=0)
+    assert e.value.status == tfmm.IO and "truncated" in str(e.value)
