@@ -140,6 +140,8 @@ struct FusedShape {
     int K1 = 0, K2 = 0;      // r_phi and r_theta padded to 16 (the two contraction depths)
     int N1p = 0, N1s = 0;    // largest r_theta x (RHS per CTA), padded to 16 (MMA N) and 32 (TMEM spacing)
     int ntp = 0, nt32 = 0;   // n_theta padded to 16 (MMA N) and 32 (TMEM spacing)
+    int nbuf = 2;            // AG4 accumulator sets in flight (1 or 2)
+    int nacc = 1;            // accumulators per set (1 or 2), each 2 ntp columns [re | im]
     int tcols = 0;           // TMEM columns per CTA
     size_t smem = 0;         // dynamic shared memory per CTA
 };

@@ -58,6 +58,8 @@ constexpr long kWaitLimit = 1L << 26;
 enum TcStage { TAG1, TAG2, TAG3, TAG4, TDG1A, TDG1B, TDG2, TDG3 };
 
 struct TcCtx {
+    const float2* spec_in;  // DG1a input (spectra; null: A from prepared planes)
+    const float* w;         // DG1a quadrature weights (null: none)
     float2* spec;        // AG4 output (spectra)
     float2* y;           // DG3 output
     const int* grp_rwg;
@@ -80,6 +82,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t (&v)[32], uint32_t taddr) {
           "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
           "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
         : "r"(taddr));
+}
+
+// 8 consecutive TMEM columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_ld8(uint32_t (&v)[8], uint32_t taddr) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr));
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -114,15 +123,31 @@ __device__ __forceinline__ void cp16(void* dst, const void* src, int bytes) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(bytes));
 }
 
-// v = t0 + t1 (+ t2) in bfloat16 terms
+// v = t0 + t1 (+ t2) in bfloat16 terms, each term as the high half of a 32-bit
+// word (the bfloat16 bit pattern): round the magnitude to 8 significant bits by
+// adding half a unit of the 16 dropped bits, subtract exactly, repeat.  Three
+// terms hold every FP32 value exactly (8 + 8 + 8 significant bits).
+template <int T>
+__device__ __forceinline__ void split_bits(float v, uint32_t* t) {
+    const uint32_t h = (__float_as_uint(v) + 0x8000u) & 0xffff0000u;
+    t[0] = h;
+    const float r = v - __uint_as_float(h);
+    const uint32_t m = (__float_as_uint(r) + 0x8000u) & 0xffff0000u;
+    t[1] = m;
+    if (T == 3) t[2] = (__float_as_uint(r - __uint_as_float(m)) + 0x8000u) & 0xffff0000u;
+}
+
 template <int T>
 __device__ __forceinline__ void split_terms(float v, bf16* t) {
-    const bf16 h = __float2bfloat16_rn(v);
-    t[0] = h;
-    const float r1 = v - __bfloat162float(h);
-    const bf16 m = __float2bfloat16_rn(r1);
-    t[1] = m;
-    if (T == 3) t[2] = __float2bfloat16_rn(r1 - __bfloat162float(m));
+    uint32_t b[3];
+    split_bits<T>(v, b);
+#pragma unroll
+    for (int q = 0; q < T; ++q) t[q] = __ushort_as_bfloat16((unsigned short)(b[q] >> 16));
+}
+
+// two split values -> one word per term plane (lower index in the low half)
+__device__ __forceinline__ uint32_t pack_hi(uint32_t lo_word, uint32_t hi_word) {
+    return __byte_perm(lo_word, hi_word, 0x7632);
 }
 
 template <int T>
@@ -137,9 +162,59 @@ __device__ __forceinline__ void store_planes(bf16* base, int64_t ps, int64_t idx
     }
 }
 
-// Loads k-tile `kt` of the problem's A (128 rows from m0) and B (BN rows from n0) into one stage.
+// DG1a A operand straight from the FP32 spectra: row m = i_phi + n_phi r, depth
+// i_theta; each element conj(W g) (Fig. 3b step 1 with the quadrature weights),
+// split into BF16 terms in registers.  Plain loads: the data pass through once.
 template <int T>
-__device__ __forceinline__ void load_stage(uint8_t* st, const TcProb& p, int m0, int n0, int kt, int kt0) {
+__device__ __forceinline__ void load_g_tile(uint8_t* st, const TcCtx& c, const TcProb& p, int m0, int k0) {
+    constexpr int ITER = TBM * 4 / TTHREADS;
+    const int nt = c.n_theta;
+    float2 v[ITER][8];
+    // every load of this thread first (memory-level parallelism), then the splits
+#pragma unroll
+    for (int i = 0; i < ITER; ++i) {
+        const int idx = threadIdx.x + i * TTHREADS, r = idx >> 2, kc = idx & 3;
+        const int m = m0 + r, k = k0 + kc * 8;
+        const bool row_ok = m < p.M;
+        const int ip = row_ok ? m % p.n_phi : 0, rr = row_ok ? m / p.n_phi : 0;
+        const int64_t o = (((int64_t)rr * c.G + p.g) * 2 + p.alpha) * c.n_dir + (int64_t)nt * ip;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int th = k + e;
+            v[i][e] = make_float2(0.f, 0.f);
+            if (row_ok && th < nt) {
+                const float2 g = __ldg(c.spec_in + o + th);
+                const float wt = c.w ? __ldg(c.w + th + (int64_t)nt * ip) : 1.0f;
+                v[i][e] = make_float2(wt * g.x, -wt * g.y);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < ITER; ++i) {
+        const int idx = threadIdx.x + i * TTHREADS, r = idx >> 2, kc = idx & 3;
+        uint32_t w[2 * T][4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+            uint32_t r0[3], i0[3], r1[3], i1[3];
+            split_bits<T>(v[i][e].x, r0); split_bits<T>(v[i][e].y, i0);
+            split_bits<T>(v[i][e + 1].x, r1); split_bits<T>(v[i][e + 1].y, i1);
+#pragma unroll
+            for (int q = 0; q < T; ++q) {
+                w[q][e / 2] = pack_hi(r0[q], r1[q]);
+                w[T + q][e / 2] = pack_hi(i0[q], i1[q]);
+            }
+        }
+        const int off = (r >> 3) * 512 + kc * 128 + (r & 7) * 16;
+#pragma unroll
+        for (int q = 0; q < 2 * T; ++q)
+            *reinterpret_cast<uint4*>(st + q * PLANE_TILE + off) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+    }
+}
+
+// Loads k-tile `kt` of the problem's A (128 rows from m0) and B (BN rows from n0) into one stage.
+template <int T, int S>
+__device__ __forceinline__ void load_stage(uint8_t* st, const TcCtx& c, const TcProb& p, int m0, int n0, int kt,
+                                           int kt0) {
     const bool seg1 = kt >= kt0;
     const int k0 = (seg1 ? kt - kt0 : kt) * TBK;
     const int K = seg1 ? p.K1 : p.K0;
@@ -148,7 +223,8 @@ __device__ __forceinline__ void load_stage(uint8_t* st, const TcProb& p, int m0,
     const bf16* B = seg1 ? p.B1 : p.B0;
     const int64_t ald = seg1 ? p.a_ld1 : p.a_ld0, aps = seg1 ? p.a_ps1 : p.a_ps0;
     const int64_t bld = seg1 ? p.b_ld1 : p.b_ld0, bps = seg1 ? p.b_ps1 : p.b_ps0;
-    const int na = 2 * T * TBM * 4;
+    const int na = (S == TDG1A && c.spec_in) ? 0 : 2 * T * TBM * 4;
+    if (S == TDG1A && c.spec_in) load_g_tile<T>(st, c, p, m0, k0);
     for (int idx = threadIdx.x; idx < na; idx += TTHREADS) {
         const int pl = idx / (TBM * 4), rem = idx % (TBM * 4), r = rem >> 2, kc = rem & 3;
         const int m = m0 + r, k = k0 + kc * 8;
@@ -245,7 +321,7 @@ __global__ void __launch_bounds__(TTHREADS) tc_gemm_kernel(const TcCtx c, const 
     bool ok = true;
     // prologue: k-tiles 0 .. NST-2
     for (int s = 0; s < NST - 1; ++s) {
-        if (s < KT) load_stage<T>(smem + s * STAGE, p, t.m0, t.n0, s, kt0);
+        if (s < KT) load_stage<T, S>(smem + s * STAGE, c, p, t.m0, t.n0, s, kt0);
         asm volatile("cp.async.commit_group;");
     }
     (void)STAGE;
@@ -253,7 +329,7 @@ __global__ void __launch_bounds__(TTHREADS) tc_gemm_kernel(const TcCtx c, const 
         const int b = kt % NST;
         if (NST == 1) {  // single buffer: reload it once the previous k-tile's MMAs are done
             if (kt >= 1) ok = ok && mbar_wait(&mbar[0], (kt - 1) & 1);
-            if (ok) load_stage<T>(smem, p, t.m0, t.n0, kt, kt0);
+            if (ok) load_stage<T, S>(smem, c, p, t.m0, t.n0, kt, kt0);
             asm volatile("cp.async.commit_group;");
             asm volatile("cp.async.wait_group 0;");
         } else if (NST == 2) {
@@ -293,7 +369,7 @@ __global__ void __launch_bounds__(TTHREADS) tc_gemm_kernel(const TcCtx c, const 
             const int nk = kt + NST - 1;
             if (nk < KT) {
                 if (kt >= 1) ok = ok && mbar_wait(&mbar[(kt - 1) % NST], ((kt - 1) / NST) & 1);
-                if (ok) load_stage<T>(smem + (nk % NST) * STAGE, p, t.m0, t.n0, nk, kt0);
+                if (ok) load_stage<T, S>(smem + (nk % NST) * STAGE, c, p, t.m0, t.n0, nk, kt0);
             }
             asm volatile("cp.async.commit_group;");
         }
@@ -326,7 +402,7 @@ __global__ void __launch_bounds__(TTHREADS) tc_gemm_kernel(const TcCtx c, const 
                 }
             }
             if (row < p.M) {
-#pragma unroll 8
+#pragma unroll
                 for (int jj = 0; jj < 32; ++jj) {
                     const int col = t.n0 + c0 + jj;
                     if (c0 + jj < p.BN && col < p.N)
@@ -372,7 +448,7 @@ __device__ __forceinline__ void load_planes(uint8_t* dst, int plane_bytes, int K
                                             int64_t ps, int rows, int valid, int kvalid) {
     const int kc8 = K / 8, k8v = (kvalid + 7) / 8;
     const int total = 2 * T * rows * kc8;
-    for (int idx = threadIdx.x; idx < total; idx += TTHREADS) {
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
         const int pl = idx / (rows * kc8), rem = idx % (rows * kc8), r = rem / kc8, kc = rem % kc8;
         const bool ok = r < valid && kc < k8v;
         const bf16* g = ok ? src + pl * ps + (int64_t)r * ld + kc * 8 : src;
@@ -386,16 +462,42 @@ __device__ __forceinline__ void issue_products(uint32_t d_re, uint32_t d_im, uin
                                                uint32_t idesc) {
     constexpr int PI[6] = {0, 0, 1, 0, 1, 2}, PJ[6] = {0, 1, 0, 2, 1, 0};
     const uint32_t idesc_neg = idesc | (1u << 13);
+    // the start-address field holds addr >> 4 (shared memory < 256 KB): offsets add to it
+    const uint64_t da = make_desc_sbo(a, sbo_a), db = make_desc_sbo(b, sbo_b);
+    const uint32_t ta = (uint32_t)T * a_plane >> 4, tb = (uint32_t)T * b_plane >> 4;
     for (int ks = 0; ks < ksteps; ++ks)
 #pragma unroll
         for (int q = 0; q < n_products<T>(); ++q) {
-            const uint32_t ar = a + PI[q] * a_plane + ks * 256, ai = a + (T + PI[q]) * a_plane + ks * 256;
-            const uint32_t br = b + PJ[q] * b_plane + ks * 256, bi = b + (T + PJ[q]) * b_plane + ks * 256;
+            const uint64_t ar = da + (uint32_t)(PI[q] * a_plane + ks * 256) / 16, ai = ar + ta;
+            const uint64_t br = db + (uint32_t)(PJ[q] * b_plane + ks * 256) / 16, bi = br + tb;
             const uint32_t acc = (ks > 0 || q > 0) ? 1u : 0u;
-            mma_bf16(d_re, make_desc_sbo(ar, sbo_a), make_desc_sbo(br, sbo_b), idesc, acc);
-            mma_bf16(d_re, make_desc_sbo(ai, sbo_a), make_desc_sbo(bi, sbo_b), idesc_neg, 1u);
-            mma_bf16(d_im, make_desc_sbo(ar, sbo_a), make_desc_sbo(bi, sbo_b), idesc, acc);
-            mma_bf16(d_im, make_desc_sbo(ai, sbo_a), make_desc_sbo(br, sbo_b), idesc, 1u);
+            mma_bf16(d_re, ar, br, idesc, acc);
+            mma_bf16(d_re, ai, bi, idesc_neg, 1u);
+            mma_bf16(d_im, ar, bi, idesc, acc);
+            mma_bf16(d_im, ai, br, idesc, 1u);
+        }
+}
+
+// Complex products with the real and imaginary parts side by side in an
+// accumulator of 2N columns: B holds per term q three planes of N rows,
+// (-Im_q, Re_q, Im_q), so rows [Re_q; Im_q] and [-Im_q; Re_q] are each one
+// 2N-row operand.  d0 += Ar [Br | Bi], d1 += Ai [-Bi | Br]; d0 + d1 is the
+// product (d1 may equal d0).
+template <int T>
+__device__ __forceinline__ void issue_products_cat(uint32_t d0, uint32_t d1, uint32_t a, int a_plane, uint32_t b,
+                                                   int b_slot, uint32_t sbo_a, uint32_t sbo_b, int ksteps,
+                                                   uint32_t idesc) {
+    constexpr int PI[6] = {0, 0, 1, 0, 1, 2}, PJ[6] = {0, 1, 0, 2, 1, 0};
+    const uint64_t da = make_desc_sbo(a, sbo_a), db = make_desc_sbo(b, sbo_b);
+    const uint32_t ta = (uint32_t)T * a_plane >> 4;
+    for (int ks = 0; ks < ksteps; ++ks)
+#pragma unroll
+        for (int q = 0; q < n_products<T>(); ++q) {
+            const uint64_t ar = da + (uint32_t)(PI[q] * a_plane + ks * 256) / 16, ai = ar + ta;
+            const uint64_t bneg = db + (uint32_t)(3 * PJ[q] * b_slot + ks * 256) / 16, bpos = bneg + b_slot / 16;
+            const uint32_t acc = (ks > 0 || q > 0) ? 1u : 0u;
+            mma_bf16(d0, ar, bpos, idesc, acc);
+            mma_bf16(d1, ai, bneg, idesc, d1 == d0 ? 1u : acc);
         }
 }
 
@@ -407,129 +509,187 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar)));
 }
 
+constexpr int F34_WORKERS = 512;               // 16 warps, four per TMEM lane quarter
+constexpr int F34_THREADS = F34_WORKERS + 32;  // and one warp that only issues MMAs
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void workers_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(F34_WORKERS) : "memory");
+}
+
+// mbarriers of the fused kernel
+enum { F34_D1 = 0, F34_A2 = 1, F34_D2 = 3, F34_EMPTY = 5, F34_NBAR = 7 };
+
 template <int T>
-__global__ void __launch_bounds__(TTHREADS) tc_ag34_kernel(const TcCtx c, const F34Item* __restrict__ items,
-                                                          const F34Tile* __restrict__ tiles, const FusedShape sh,
-                                                          int n_phi) {
+__global__ void __launch_bounds__(F34_THREADS) tc_ag34_kernel(const TcCtx c, const F34Item* __restrict__ items,
+                                                             const F34Tile* __restrict__ tiles, const FusedShape sh,
+                                                             int n_phi) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t mbar[3];  // AG3 done, D2 buffer 0, D2 buffer 1
+    // F34_D1: AG3 done; F34_A2 + b: A2[b] written; F34_D2 + b: AG4 into D2[b] done;
+    // F34_EMPTY + b: D2[b] read out
+    __shared__ __align__(8) uint64_t mbar[F34_NBAR];
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const F34Tile t = tiles[blockIdx.x];
     const F34Item it = items[t.item];
     const int K1 = sh.K1, K2 = sh.K2, nt = c.n_theta;
     const int a1p = TBM * K1 * 2, b1p = sh.N1p * K1 * 2, b2p = sh.ntp * K2 * 2, a2p = TBM * K2 * 2;
+    // U_phi and M' are dead once AG3 is done: the spectra staging reuses the first,
+    // the two A operands of AG4 the second
+    const int r1 = max(2 * T * a1p, n_phi * nt * 8), r2 = max(2 * T * b1p, 2 * 2 * T * a2p);
     uint8_t* sA1 = smem;
-    uint8_t* sB1 = sA1 + 2 * T * a1p;
-    uint8_t* sB2 = sB1 + 2 * T * b1p;
-    uint8_t* sA2 = sB2 + 2 * T * b2p;
+    float2* stage = reinterpret_cast<float2*>(smem);
+    uint8_t* sB1 = smem + r1;
+    uint8_t* sA2b = sB1;
+    uint8_t* sB2 = sB1 + r2;  // 3T slots (-Im_q, Re_q, Im_q) of b2p bytes
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
                      "r"(sh.tcols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0)
-        for (int b = 0; b < 3; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[b])), "r"(1));
+        for (int b = 0; b < F34_NBAR; ++b) {
+            const int cnt = (b == F34_A2 || b == F34_A2 + 1 || b == F34_EMPTY || b == F34_EMPTY + 1) ? F34_WORKERS : 1;
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[b])), "r"(cnt));
+        }
     asm volatile("fence.mbarrier_init.release.cluster;");
     const int n1 = it.rt * t.nr, n1p = (n1 + 15) & ~15;
     load_planes<T>(sA1, a1p, K1, it.uph, it.uph_ld, it.uph_ps, n_phi, n_phi, it.rp);
     load_planes<T>(sB1, b1p, K1, it.m + (int64_t)it.rt * t.r0 * it.m_ld, it.m_ld, it.m_ps, n1p, n1, it.rp);
-    load_planes<T>(sB2, b2p, K2, it.uth, it.uth_ld, it.uth_ps, sh.ntp, nt, it.rt);
+    for (int q = 0; q < T; ++q) {  // Re_q -> slot 3q + 1, Im_q -> slot 3q + 2
+        load_planes<1>(sB2 + (3 * q + 1) * b2p, b2p, K2, it.uth + q * it.uth_ps, it.uth_ld, it.uth_ps * T, sh.ntp,
+                       nt, it.rt);
+    }
     asm volatile("cp.async.commit_group;");
     asm volatile("cp.async.wait_group 0;");
+    __syncthreads();
+    for (int q = 0; q < T; ++q) {  // slot 3q = -Im_q (bfloat16 sign bits flipped)
+        const uint4* src = reinterpret_cast<const uint4*>(sB2 + (3 * q + 2) * b2p);
+        uint4* dst = reinterpret_cast<uint4*>(sB2 + 3 * q * b2p);
+        for (int e = tid; e < b2p / 16; e += F34_THREADS) {
+            const uint4 v = src[e];
+            dst[e] = make_uint4(v.x ^ 0x80008000u, v.y ^ 0x80008000u, v.z ^ 0x80008000u, v.w ^ 0x80008000u);
+        }
+    }
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tm = tmem_base;
-    const uint32_t lanes = (uint32_t)(warp * 32) << 16;
-    const uint32_t d2 = tm + 2 * sh.N1s;  // D2 buffer b: re at d2 + 2 b nt32, im at + nt32
-    if (tid == 0)
-        issue_products<T>(tm, tm + sh.N1s, smem_u32(sA1), a1p, smem_u32(sB1), b1p, K1 * 16, K1 * 16, K1 / 16,
-                          idesc_bf16(n1p));
-    if (tid == 0) mma_commit(&mbar[0]);
-    bool ok = mbar_wait(&mbar[0], 0);
-    bool ag3_done = __syncthreads_and(ok);
-    ok = ag3_done;
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    const int phi = warp * 32 + lane;
-    const int64_t n_dir = c.n_dir;
-    int issued = -1;
-    for (int j = 0; j <= t.nr && ok; ++j) {
-        if (j > 0) {  // MMAs of j - 1 done: A2 is free and D2[(j-1)&1] holds F_{j-1}
-            const bool w = mbar_wait(&mbar[1 + ((j - 1) & 1)], ((j - 1) >> 1) & 1);
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            ok = __syncthreads_and(w);
-            if (!ok) break;
-        }
-        if (j < t.nr) {
-            // V_j: TMEM columns (a + r_t j) -> BF16 planes of A2, row i_phi, depth a (zeros past r_t)
-            for (int c0 = 0; c0 < K2; c0 += 32) {
-                uint32_t vr[32], vi[32];
-                tmem_ld32(vr, tm + lanes + it.rt * j + c0);
-                tmem_ld32(vi, tm + lanes + sh.N1s + it.rt * j + c0);
-                asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-                for (int k8 = 0; k8 < 32; k8 += 8) {
-                    if (c0 + k8 >= K2) break;
-                    uint32_t w[2 * T][4];
-#pragma unroll
-                    for (int e = 0; e < 8; e += 2) {
-                        bf16 tr0[3], ti0[3], tr1[3], ti1[3];
-                        const int k = c0 + k8 + e;
-                        const float r0 = k < it.rt ? __uint_as_float(vr[k8 + e]) : 0.f;
-                        const float i0 = k < it.rt ? __uint_as_float(vi[k8 + e]) : 0.f;
-                        const float r1 = k + 1 < it.rt ? __uint_as_float(vr[k8 + e + 1]) : 0.f;
-                        const float i1 = k + 1 < it.rt ? __uint_as_float(vi[k8 + e + 1]) : 0.f;
-                        split_terms<T>(r0, tr0); split_terms<T>(i0, ti0);
-                        split_terms<T>(r1, tr1); split_terms<T>(i1, ti1);
-#pragma unroll
-                        for (int q = 0; q < T; ++q) {
-                            w[q][e / 2] = (uint32_t)__bfloat16_as_ushort(tr0[q]) |
-                                          ((uint32_t)__bfloat16_as_ushort(tr1[q]) << 16);
-                            w[T + q][e / 2] = (uint32_t)__bfloat16_as_ushort(ti0[q]) |
-                                              ((uint32_t)__bfloat16_as_ushort(ti1[q]) << 16);
-                        }
-                    }
-                    const int off = (phi >> 3) * (K2 * 16) + ((c0 + k8) >> 3) * 128 + (phi & 7) * 16;
-#pragma unroll
-                    for (int q = 0; q < 2 * T; ++q)
-                        *reinterpret_cast<uint4*>(sA2 + q * a2p + off) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
-                }
-            }
-            asm volatile("fence.proxy.async.shared::cta;");
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            __syncthreads();
-            if (tid == 0) {
+    // AG4 accumulator set b at d2 + b set: [re | im] of d0, then (two accumulators) of d1
+    const uint32_t d2 = tm + 2 * sh.N1s;
+    const int nbuf = sh.nbuf, set = 2 * sh.nacc * sh.ntp;
+    bool ok = true;
+    if (warp == F34_WORKERS / 32) {
+        // ---- MMA warp: AG3 once, then AG4 for every r as soon as its A2 is written
+        if (lane == 0) {
+            issue_products<T>(tm, tm + sh.N1s, smem_u32(sA1), a1p, smem_u32(sB1), b1p, K1 * 16, K1 * 16, K1 / 16,
+                              idesc_bf16(n1p));
+            mma_commit(&mbar[F34_D1]);
+            for (int j = 0; j < t.nr; ++j) {
+                const int a = j & 1, b = j % nbuf;
+                ok = mbar_wait(&mbar[F34_A2 + a], (j >> 1) & 1) && ok;
+                if (j >= nbuf) ok = mbar_wait(&mbar[F34_EMPTY + b], ((j - nbuf) / nbuf) & 1) && ok;
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t dr = d2 + 2 * (j & 1) * sh.nt32;
-                issue_products<T>(dr, dr + sh.nt32, smem_u32(sA2), a2p, smem_u32(sB2), b2p, K2 * 16, K2 * 16, K2 / 16,
-                                  idesc_bf16(sh.ntp));
-                mma_commit(&mbar[1 + (j & 1)]);
+                const uint32_t dr = d2 + b * set;
+                issue_products_cat<T>(dr, dr + (sh.nacc - 1) * 2 * sh.ntp, smem_u32(sA2b + a * 2 * T * a2p), a2p,
+                                      smem_u32(sB2), b2p,
+                                      K2 * 16, K2 * 16, K2 / 16, idesc_bf16(2 * sh.ntp));
+                mma_commit(&mbar[F34_D2 + b]);
             }
-            issued = j;
         }
-        if (j > 0) {  // spectra of RHS r0 + j - 1, straight from TMEM
-            const uint32_t dr = d2 + 2 * ((j - 1) & 1) * sh.nt32;
-            const int r = t.r0 + j - 1;
-            float2* F = c.spec + (((int64_t)r * c.G + it.g) * 2 + it.alpha) * n_dir + (int64_t)nt * phi;
-            for (int c0 = 0; c0 < sh.ntp; c0 += 32) {
-                uint32_t vr[32], vi[32];
-                tmem_ld32(vr, dr + lanes + c0);
-                tmem_ld32(vi, dr + lanes + sh.nt32 + c0);
-                asm volatile("tcgen05.wait::ld.sync.aligned;");
-                if (phi < n_phi) {
-#pragma unroll 8
-                    for (int e = 0; e < 32; ++e)
-                        if (c0 + e < nt) F[c0 + e] = make_float2(__uint_as_float(vr[e]), __uint_as_float(vi[e]));
+        __syncwarp();
+    } else {
+        // ---- workers: warps w, w + 4, ... share lane quarter w & 3 and split the columns
+        const int phi = (warp & 3) * 32 + lane, grp = warp >> 2, ngrp = F34_WORKERS / 128;
+        const bool rows = (warp & 3) * 32 < n_phi;  // quarters past n_phi hold no direction
+        const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+        const int64_t n_dir = c.n_dir;
+        ok = mbar_wait(&mbar[F34_D1], 0);
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        for (int j = 0; j <= t.nr; ++j) {
+            if (j < t.nr) {
+                // V_j: TMEM columns (a + r_t j) -> BF16 planes of A2[j & 1], row i_phi, depth a
+                // (zeros past r_t); A2[j & 1] was last read by the MMAs of j - 2, waited below
+                uint8_t* sA2 = sA2b + (j & 1) * 2 * T * a2p;
+                if (rows)
+                    for (int kc = grp; kc < K2 / 8; kc += ngrp) {
+                        const int off = (phi >> 3) * (K2 * 16) + kc * 128 + (phi & 7) * 16;
+                        if (kc * 8 >= it.rt) {
+#pragma unroll
+                            for (int q = 0; q < 2 * T; ++q)
+                                *reinterpret_cast<uint4*>(sA2 + q * a2p + off) = make_uint4(0, 0, 0, 0);
+                            continue;
+                        }
+                        uint32_t vr[8], vi[8], w[2 * T][4];
+                        tmem_ld8(vr, tm + lanes + it.rt * j + kc * 8);
+                        tmem_ld8(vi, tm + lanes + sh.N1s + it.rt * j + kc * 8);
+                        asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+                        for (int e = 0; e < 8; e += 2) {
+                            uint32_t tr0[3], ti0[3], tr1[3], ti1[3];
+                            const int k = kc * 8 + e;
+                            split_bits<T>(k < it.rt ? __uint_as_float(vr[e]) : 0.f, tr0);
+                            split_bits<T>(k < it.rt ? __uint_as_float(vi[e]) : 0.f, ti0);
+                            split_bits<T>(k + 1 < it.rt ? __uint_as_float(vr[e + 1]) : 0.f, tr1);
+                            split_bits<T>(k + 1 < it.rt ? __uint_as_float(vi[e + 1]) : 0.f, ti1);
+#pragma unroll
+                            for (int q = 0; q < T; ++q) {
+                                w[q][e / 2] = pack_hi(tr0[q], tr1[q]);
+                                w[T + q][e / 2] = pack_hi(ti0[q], ti1[q]);
+                            }
+                        }
+#pragma unroll
+                        for (int q = 0; q < 2 * T; ++q)
+                            *reinterpret_cast<uint4*>(sA2 + q * a2p + off) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+                    }
+                asm volatile("fence.proxy.async.shared::cta;");
+                mbar_arrive(&mbar[F34_A2 + (j & 1)]);
+            }
+            if (j > 0) {
+                // spectra of RHS r0 + j - 1: TMEM -> rows in shared memory -> one contiguous block
+                const int jj = j - 1, b = jj % nbuf;
+                ok = mbar_wait(&mbar[F34_D2 + b], (jj / nbuf) & 1) && ok;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t dr = d2 + b * set;
+                for (int kc = grp; rows && kc < sh.ntp / 8; kc += ngrp) {
+                    uint32_t vr[8], vi[8], ur[8] = {}, ui[8] = {};
+                    tmem_ld8(vr, dr + lanes + kc * 8);
+                    tmem_ld8(vi, dr + lanes + sh.ntp + kc * 8);
+                    if (sh.nacc == 2) {
+                        tmem_ld8(ur, dr + lanes + 2 * sh.ntp + kc * 8);
+                        tmem_ld8(ui, dr + lanes + 3 * sh.ntp + kc * 8);
+                    }
+                    asm volatile("tcgen05.wait::ld.sync.aligned;");
+                    if (phi < n_phi) {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e)
+                            if (kc * 8 + e < nt)
+                                stage[phi * nt + kc * 8 + e] =
+                                    make_float2(__uint_as_float(vr[e]) + __uint_as_float(ur[e]),
+                                                __uint_as_float(vi[e]) + __uint_as_float(ui[e]));
+                    }
                 }
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                mbar_arrive(&mbar[F34_EMPTY + b]);  // set b may take the MMAs of jj + nbuf
+                workers_sync();
+                float2* F = c.spec + (((int64_t)(t.r0 + jj) * c.G + it.g) * 2 + it.alpha) * n_dir;
+                if ((n_dir & 1) == 0) {
+                    const float4* src = reinterpret_cast<const float4*>(stage);
+                    float4* dst = reinterpret_cast<float4*>(F);
+                    for (int e = tid; e < (int)(n_dir >> 1); e += F34_WORKERS) dst[e] = src[e];
+                } else {
+                    for (int e = tid; e < (int)n_dir; e += F34_WORKERS) F[e] = stage[e];
+                }
+                workers_sync();
             }
         }
     }
-    // no MMA may still run when TMEM is freed
-    if (!ag3_done) mbar_wait(&mbar[0], 0);
-    else if (issued >= 0 && !ok) mbar_wait(&mbar[1 + (issued & 1)], (issued >> 1) & 1);
-    if (!ok && tid == 0) atomicAdd(c.err, 1);
+    // every MMA was waited for (bounded) by the workers before TMEM is freed
+    if (!ok) atomicAdd(c.err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(sh.tcols));
@@ -727,15 +887,17 @@ void upload_tc_stage(TcStagePlan& st, const std::vector<TcProb>& probs, const st
 bool fused_enabled() {
     static const bool on = [] {
         const char* e = std::getenv("TFMM_TC_FUSED");
-        return e && e[0] == '1';
+        return !(e && e[0] == '0');
     }();
     return on;
 }
 
 constexpr size_t kMaxDynSmem = 225 * 1024;
 
-size_t f34_smem(int T, int K1, int K2, int N1p, int ntp) {
-    return (size_t)2 * T * 2 * ((size_t)TBM * K1 + (size_t)N1p * K1 + (size_t)ntp * K2 + (size_t)TBM * K2);
+size_t f34_smem(int T, int K1, int K2, int N1p, int ntp, int nt, int np) {
+    const size_t pl = (size_t)2 * T * 2;  // bytes per element over the 2T planes
+    return std::max(pl * TBM * K1, (size_t)np * nt * 8) + pl * std::max((size_t)N1p * K1, (size_t)2 * TBM * K2) +
+           (size_t)3 * T * 2 * ntp * K2;
 }
 
 // Shapes and work list of the fused AG3 + AG4 kernel; leaves M.fused34 false
@@ -745,15 +907,22 @@ void plan_fused34(const Plan& P, TcPlan& M, const bf16* F, const std::vector<TcI
     M.fused34 = false;
     if (!fused_enabled()) return;
     const int T = M.T, R = M.R, nt = P.n_theta, np = P.n_phi;
-    if (np > TBM || nt > 256) return;
+    if (np > TBM || nt > 128) return;  // lanes; AG4 runs as one MMA of N = 2 n_theta (<= 256)
     FusedShape f;
     f.K1 = (P.max_rank[1] + 15) & ~15;
     f.K2 = (P.max_rank[0] + 15) & ~15;
     f.ntp = (nt + 15) & ~15;
     f.nt32 = (nt + 31) & ~31;
-    const int n1s_cap = ((512 - 4 * f.nt32) / 2) & ~31;
+    // two AG4 accumulator sets in flight (the MMAs of r overlap the spectra of r - 1), one
+    // accumulator each; both are tuning knobs
+    f.nbuf = 2;
+    f.nacc = 1;
+    if (const char* e = std::getenv("TFMM_TC_F34_NBUF")) f.nbuf = (std::atoi(e) == 1) ? 1 : 2;
+    if (const char* e = std::getenv("TFMM_TC_F34_NACC")) f.nacc = (std::atoi(e) == 2) ? 2 : 1;
+    const int n1s_cap = ((512 - f.nbuf * 2 * f.nacc * f.ntp) / 2) & ~31;
     int n1max = std::min(256, n1s_cap);
-    while (n1max >= 16 && f34_smem(T, f.K1, f.K2, n1max, f.ntp) > kMaxDynSmem) n1max -= 16;
+    if (const char* e = std::getenv("TFMM_TC_F34_N1")) n1max = std::min(n1max, std::max(16, std::atoi(e)) & ~15);
+    while (n1max >= 16 && f34_smem(T, f.K1, f.K2, n1max, f.ntp, nt, np) > kMaxDynSmem) n1max -= 16;
     if (n1max < ((P.max_rank[0] + 15) & ~15)) return;
     std::vector<F34Item> items(P.items.size());
     std::vector<int> nr_of(P.items.size());
@@ -773,9 +942,9 @@ void plan_fused34(const Plan& P, TcPlan& M, const bf16* F, const std::vector<TcI
     f.N1p = n1p_max;
     f.N1s = (n1p_max + 31) & ~31;
     f.tcols = 32;
-    while (f.tcols < 2 * f.N1s + 4 * f.nt32) f.tcols *= 2;
+    while (f.tcols < 2 * f.N1s + f.nbuf * 2 * f.nacc * f.ntp) f.tcols *= 2;
     if (f.tcols > 512) return;
-    f.smem = f34_smem(T, f.K1, f.K2, f.N1p, f.ntp);
+    f.smem = f34_smem(T, f.K1, f.K2, f.N1p, f.ntp, nt, np);
     // no more CTAs per SM than their TMEM allocations allow
     constexpr size_t kSmemSM = 228 * 1024;
     const int ctas_tmem = 512 / f.tcols;
@@ -805,7 +974,7 @@ void launch_ag34(const Plan& P, const TcPlan& M, const TcCtx& c, cudaStream_t s)
                                              (int)kMaxDynSmem));
         attr = true;
     }
-    tc_ag34_kernel<T><<<M.f34_ntiles, TTHREADS, M.f34.smem, s>>>(
+    tc_ag34_kernel<T><<<M.f34_ntiles, F34_THREADS, M.f34.smem, s>>>(
         c, static_cast<const F34Item*>(M.f34_items.p), static_cast<const F34Tile*>(M.f34_tiles.p), M.f34, P.n_phi);
     TFMM_CUDA_CHECK(cudaGetLastError());
 }
@@ -966,11 +1135,16 @@ void tc_disaggregate_t(Plan& P, TcPlan& M, const float2* spec, int R, int weight
     c.grp_rwg = P.d_grp_rwg; c.R = R; c.G = P.G; c.n_theta = P.n_theta; c.n_dir = P.n_dir; c.err = static_cast<int*>(P.tc_err.p);
     c.ld = ldy; c.beta = beta;
     c.y = y;
-    dim3 gg(64, std::min(P.G * 2, 4096));
-    prep_g_kernel<T><<<gg, 256, 0, s>>>(spec, weights ? P.d_weights : nullptr,
-                                        reinterpret_cast<const TcProb*>(M.st[TDG1A].d_probs), M.st[TDG1A].n_probs, R,
-                                        P.G, P.n_theta, P.n_phi);
-    TFMM_CUDA_CHECK(cudaGetLastError());
+    if (fused_enabled()) {  // DG1a reads the FP32 spectra itself
+        c.spec_in = spec;
+        c.w = weights ? P.d_weights : nullptr;
+    } else {
+        dim3 gg(64, std::min(P.G * 2, 4096));
+        prep_g_kernel<T><<<gg, 256, 0, s>>>(spec, weights ? P.d_weights : nullptr,
+                                            reinterpret_cast<const TcProb*>(M.st[TDG1A].d_probs), M.st[TDG1A].n_probs,
+                                            R, P.G, P.n_theta, P.n_phi);
+        TFMM_CUDA_CHECK(cudaGetLastError());
+    }
     launch_tc<T, TDG1A>(M.st[TDG1A], c, s);
     launch_tc<T, TDG1B>(M.st[TDG1B], c, s);
     launch_tc<T, TDG2>(M.st[TDG2], c, s);

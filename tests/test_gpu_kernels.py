@@ -48,6 +48,9 @@ CASES = {
     "paper_like": (40, 80, [940, 1786, 411], lambda rng, nb: [
         (int(rng.integers(24, 31)), int(rng.integers(28, 36)), int(rng.integers(170, 201))) for _ in range(2)]),
     "odd_grid": (13, 25, [33, 50], lambda rng, nb: [(5, 7, 9), (13, 25, 33 if nb == 33 else 50)]),
+    # more phi samples than TMEM lanes: the tensor-core chain runs AG3 and AG4 apart
+    "wide": (9, 136, [60, 33], lambda rng, nb: [(int(rng.integers(1, 10)), int(rng.integers(20, 60)),
+                                                 int(rng.integers(1, nb + 1))) for _ in range(2)]),
 }
 
 
@@ -242,7 +245,7 @@ def test_multi_rhs_chain_matches_oracle(name, R):
 
 
 @pytest.mark.parametrize("terms,tol", [(3, 1e-5), (2, 5e-5)])
-@pytest.mark.parametrize("name,R", [("paper_like", 16), ("ragged", 7), ("odd_grid", 3)])
+@pytest.mark.parametrize("name,R", [("paper_like", 16), ("ragged", 7), ("odd_grid", 3), ("wide", 5)])
 def test_tensor_core_chain_matches_oracle(name, R, terms, tol):
     """tcgen05 chains with FP32 operands split into `terms` BF16 terms, FP32 accumulation."""
     tfmm = _tfmm()
