@@ -49,6 +49,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-groups", type=int, default=3)
     ap.add_argument("--graph", action="store_true", help="replay one captured CUDA graph per step")
+    ap.add_argument("--sweep", action="store_true",
+                    help="parameter sweep on the 20-lambda sphere (box x tolerance x digits, 16 RHS): "
+                         "one JSON line per point")
+    ap.add_argument("--sweep-boxes", default="0.5,1,2,4")
+    ap.add_argument("--sweep-tols", default="1e-3,1e-4,1e-6,1e-8")
+    ap.add_argument("--sweep-digits", default="3,6")
     ap.add_argument("--mrhs-precision", type=int, default=None,
                     help="R > 1: 0 FP32 CUDA cores, 2 / 3 tensor cores with 2- / 3-term split BF16 (default 3)")
     return ap.parse_args()
@@ -485,8 +491,122 @@ def run_ours(args, w, world, rank, local):
         dist.destroy_process_group()
 
 
+def run_sweep(args):
+    """Box size x Tucker tolerance x digits on the 20-lambda sphere with 16 CN(0,1) RHS.
+
+    Per point: setup, autotuner (R = 16), event-timed aggregation + disaggregation,
+    compression, roofline fractions, and the per-RHS error of the aggregation against the
+    oracle's own FP64 far-fields and dense Eq. 3 on the two smallest groups.
+    """
+    import torch
+    import oracle
+    from oracle import apply
+    from paper_2103_05822_gb300 import tfmm
+    from paper_2103_05822_gb300.inputs import WORKLOADS, complex_gaussian, icosphere
+    w = WORKLOADS["sphere20_sweep"]
+    R = w.nrhs
+    verts, tris = icosphere(w.diameter, w.nu)
+    mesh = tfmm.tfmm_mesh_create(verts, tris)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    tensor = peaks.get("bf16_tflops_sustained", 1700.0)
+    fp32 = 152 * 128 * 2 * 2.07e9 / 1e12
+    stream = torch.cuda.current_stream()
+    oracle_cache = {}
+    boxes = [float(v) for v in args.sweep_boxes.split(",")]
+    tols = [float(v) for v in args.sweep_tols.split(",")]
+    digits = [int(v) for v in args.sweep_digits.split(",")]
+    for d0 in digits:
+        for box in sorted(boxes):
+            for tol in sorted(tols, reverse=True):
+                t0 = time.perf_counter()
+                prm = tfmm.tfmm_params_default(k=2 * math.pi, box=box, digits=float(d0), tol=tol, max_rhs=R,
+                                               mrhs_precision=3)
+                plan = tfmm.tfmm_plan_create(mesh, prm, stream=stream)
+                setup_s = time.perf_counter() - t0
+                info = plan.info
+                N, G, nd = info["n_rwg"], info["n_groups"], info["n_dir"]
+                tune = tfmm.tfmm_autotune(plan, R=R, budget_ms=3000.0, stream=stream)
+                X = complex_gaussian((R, N), w.seed)
+                x = torch.from_numpy(X.astype(np.complex64)).cuda()
+                spec = torch.empty((R, G, 2, nd), dtype=torch.complex64, device="cuda")
+                y = torch.empty((R, N), dtype=torch.complex64, device="cuda")
+                for _ in range(3):
+                    tfmm.tfmm_aggregate(plan, x, spec, stream=stream)
+                    tfmm.tfmm_disaggregate(plan, spec, y, stream=stream)
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                agg, dis = [], []
+                for _ in range(10):
+                    ev[0].record(stream)
+                    tfmm.tfmm_aggregate(plan, x, spec, stream=stream)
+                    ev[1].record(stream)
+                    tfmm.tfmm_disaggregate(plan, spec, y, stream=stream)
+                    ev[2].record(stream)
+                    torch.cuda.synchronize()
+                    agg.append(ev[0].elapsed_time(ev[1]))
+                    dis.append(ev[1].elapsed_time(ev[2]))
+                tfmm.tfmm_sync(plan, stream=stream)
+                a_ms, d_ms = statistics.median(agg), statistics.median(dis)
+                cm = 0
+                sizes = []
+                for g in range(G):
+                    nb_g = 0
+                    for a in range(2):
+                        nb, (rt, rp, rb) = tfmm.tfmm_plan_group(plan, g, a)
+                        nb_g = nb
+                        cm += nb * rb + rt * rp * rb + info["n_phi"] * rp * rt + nd * rt
+                    sizes.append((nb_g, g))
+                flops = 8.0 * cm * R
+                fac = info["tucker_bytes_alg"]
+                bytes_agg = fac + 8 * N * R + 16 * G * nd * R
+                dense_bytes = 16 * N * nd
+                engine = {0: "fp32_chain", 1: "fp32_columns", 2: "tc_split_bf16_2", 3: "tc_split_bf16_3"}[tune["mrhs_precision"]]
+                fl_peak = tensor if tune["mrhs_precision"] in (2, 3) else fp32
+                # oracle: its own far-fields of the two smallest groups, dense FP64 Eq. 3
+                pick = [g for _, g in sorted(sizes)[:2]]
+                key = (box, d0)
+                if key not in oracle_cache:  # the far-fields do not depend on the tolerance
+                    oracle_cache.clear()
+                    oracle_cache[key] = oracle.problem.build(verts, tris, k=2 * math.pi, box=box, digits=d0, tol=tol,
+                                                             compress=False, keep_tensors=True, groups_subset=pick)
+                P = oracle_cache[key]
+                S = spec.cpu().numpy()
+                err = 0.0
+                for r in range(R):
+                    num = den = 0.0
+                    for g in pick:
+                        xg = X[r][P.groups.members[g]]
+                        A_t, A_p = P.group_tensors(g)
+                        for a, A in enumerate((A_t, A_p)):
+                            ref = apply.dense_aggregate(A, xg)
+                            num += float(np.sum(np.abs(S[r, g, a] - ref) ** 2))
+                            den += float(np.sum(np.abs(ref) ** 2))
+                    err = max(err, math.sqrt(num / den))
+                line = {
+                    "point": {"box_lambda": box, "tol": tol, "digits": d0},
+                    "L": info["L"], "n_theta": info["n_theta"], "n_phi": info["n_phi"], "groups": G,
+                    "max_rank": info["max_rank"], "max_n_beta": info["max_n_beta"],
+                    "compression": dense_bytes / fac, "tucker_gb": fac / 1e9, "dense_gb": dense_bytes / 1e9,
+                    "ms_per_matvec": a_ms + d_ms, "aggregate_ms": a_ms, "disaggregate_ms": d_ms,
+                    "nrhs": R, "engine": engine, "tuning": tune,
+                    "hbm_frac": bytes_agg / (max(a_ms, d_ms) * 1e-3) / 1e9 / hbm,
+                    "flop_frac": flops / (max(a_ms, d_ms) * 1e-3) / 1e12 / fl_peak,
+                    "rel_err_vs_oracle_dense": err, "oracle_groups": pick, "setup_s": setup_s,
+                }
+                print(json.dumps(line), flush=True)
+                del plan, x, spec, y
+                torch.cuda.empty_cache()
+
+
 def main():
     args = parse()
+    if args.sweep:
+        run_sweep(args)
+        return
     from paper_2103_05822_gb300.inputs import WORKLOADS
     w = WORKLOADS[args.workload]
     world, rank, local = dist_env()

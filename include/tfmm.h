@@ -71,9 +71,10 @@ typedef struct {
     int32_t keep_dense;/* nonzero: also keep FP32 uncompressed tensors (Eqs. 3, 5) */
     int32_t max_rhs;   /* largest R later passed to the hot path (>= 1) */
     int32_t batch_groups; /* groups per setup batch (0 = automatic) */
-    int32_t mrhs_precision; /* R > 1: 0 = FP32 on CUDA cores; 2 or 3 = tensor cores with
-                               FP32 operands split into 2 or 3 BF16 terms (hi + lo [+ lo2]),
-                               FP32 accumulation */
+    int32_t mrhs_precision; /* engine for R > 1: 0 = grouped-GEMM chain in FP32 on CUDA cores;
+                               1 = the single-RHS kernels, one column after another (FP32);
+                               2 or 3 = tensor cores with FP32 operands split into 2 or 3
+                               BF16 terms (hi + lo [+ lo2]), FP32 accumulation */
     int32_t reserved[5];
 } tfmm_params;
 
@@ -152,7 +153,9 @@ tfmm_status tfmm_plan_from_tucker(int64_t n_rwg, int32_t n_groups, int32_t n_the
  * column-major tensor A[i_theta, i_phi, n] = P^{alpha,+}_{n,i} (Fig. 1a). */
 tfmm_status tfmm_plan_set_dense(tfmm_plan* plan, const tfmm_cdouble* tensors, void* stream);
 
-/* Arithmetic of the R > 1 hot path (see tfmm_params.mrhs_precision): 0, 2 or 3.
+/* Engine of the R > 1 hot path (see tfmm_params.mrhs_precision): 0, 1, 2 or 3.
+ * When the largest work item does not fit the single-RHS kernels (shared
+ * memory), every R, R = 1 included, runs the FP32 grouped-GEMM chain.
  * Tensor-core modes build BF16 planes of the factors on first use (device
  * memory: 2 layouts x 2 or 3 terms of every factor).  INVALID_ARG otherwise. */
 tfmm_status tfmm_plan_set_mrhs_precision(tfmm_plan* plan, int32_t precision);
@@ -309,10 +312,11 @@ tfmm_status tfmm_plan_tuning_set(tfmm_plan* plan, const tfmm_tuning* t, void* st
 /* Autotuner: times candidate settings on the plan's own factors with scratch
  * inputs (allocated and freed here; CUDA events on `stream`) and keeps the
  * fastest.  R == 1 searches launch shape and queue order of each stage; R > 1
- * chooses between the FP32 CUDA-core chain and the 3-term tensor-core chain
- * (and the 2-term one when allow_two_term != 0, which is less accurate).
- * The search stops early once budget_ms of wall time is spent.  `out` (may be
- * NULL) receives the chosen tuning.  No counterpart in the paper. */
+ * chooses the engine among the 3-term tensor-core chain, the FP32 CUDA-core
+ * chain and the single-RHS kernels column by column (and the 2-term chain
+ * when allow_two_term != 0, which is less accurate).  The search stops early
+ * once budget_ms of wall time is spent.  `out` (may be NULL) receives the
+ * chosen tuning.  No counterpart in the paper. */
 tfmm_status tfmm_autotune(tfmm_plan* plan, int32_t R, double budget_ms, int32_t allow_two_term, void* stream,
                           tfmm_tuning* out);
 

@@ -492,11 +492,16 @@ Schedule make_schedule(K kernel, int NT, size_t smem, int num_sms, int n_items, 
     Schedule s;
     s.threads = NT;
     s.smem = smem;
+    s.blocks = 0;  // 0: the largest work item does not fit one CTA
+    int dev = 0, opt_in = 0;
+    TFMM_CUDA_CHECK(cudaGetDevice(&dev));
+    TFMM_CUDA_CHECK(cudaDeviceGetAttribute(&opt_in, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (smem > (size_t)opt_in) return s;
     if (smem > 48 * 1024)
         TFMM_CUDA_CHECK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     TFMM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, NT, smem));
-    if (per_sm < 1) fail(TFMM_INVALID_ARG, "work item too large for one CTA (shared memory " + std::to_string(smem) + " B)");
+    if (per_sm < 1) return s;
     if (ctas_per_sm > 0) per_sm = std::min(per_sm, ctas_per_sm);
     s.blocks = std::max(1, std::min(per_sm * num_sms, n_items));
     return s;
@@ -611,6 +616,7 @@ void configure_hot(Plan& P, const HotTuning& t, cudaStream_t s) {
     P.dis_sched = make_schedule(tucker_disaggregate_kernel, t.dis_threads,
                                 sizeof(float2) * dis_layout(P, t.dis_threads).total, P.num_sms, P.G, t.dis_ctas_per_sm);
     P.tuning = t;
+    P.hot_ok = P.agg_sched.blocks > 0 && P.dis_sched.blocks > 0;
     TFMM_CUDA_CHECK(cudaStreamSynchronize(s));
 }
 
@@ -641,6 +647,8 @@ void finalize_dense_layout(Plan& P) {
     P.dagg_sched = make_schedule(dense_aggregate_kernel, NT, sizeof(float2) * (al16(P.max_nb) + 2 * NT), P.num_sms, nI);
     P.ddis_sched = make_schedule(dense_disaggregate_kernel, NT, sizeof(float2) * (P.ld_dir + al16(P.max_nb)),
                                  P.num_sms, P.G);
+    TFMM_REQUIRE(P.dagg_sched.blocks > 0 && P.ddis_sched.blocks > 0,
+                 "dense comparator: a group's RWGs or directions exceed one CTA's shared memory");
 }
 
 void pack_dense_fp32_from_f64(Plan& P, const double2* src, int g, int alpha, cudaStream_t s) {
@@ -651,6 +659,7 @@ void pack_dense_fp32_from_f64(Plan& P, const double2* src, int g, int alpha, cud
 }
 
 void launch_tucker_aggregate(const Plan& P, const float2* x, int R, int64_t ldx, float2* spec, cudaStream_t s) {
+    TFMM_REQUIRE(P.hot_ok, "single-RHS kernels unavailable for this plan (work item exceeds one CTA)");
     AggArgs a;
     a.items = P.d_items;
     a.order = P.d_agg_order;
@@ -674,6 +683,7 @@ void launch_tucker_aggregate(const Plan& P, const float2* x, int R, int64_t ldx,
 
 void launch_tucker_disaggregate(const Plan& P, const float2* spec, int R, int weights, float2 beta, float2* y,
                                 int64_t ldy, cudaStream_t s) {
+    TFMM_REQUIRE(P.hot_ok, "single-RHS kernels unavailable for this plan (work item exceeds one CTA)");
     DisArgs a;
     a.items = P.d_items;
     a.order = P.d_dis_order;

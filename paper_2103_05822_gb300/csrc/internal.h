@@ -209,6 +209,7 @@ struct Plan {
     std::vector<TuckerItem> items;
     Schedule agg_sched, dis_sched;
     HotTuning tuning;
+    bool hot_ok = false;               // the single-RHS kernels fit (shared memory of the largest item)
     double tuned_ms[2] = {0, 0};       // autotuner's best aggregate / disaggregate times
     int live_graphs = 0;               // captured graphs that still point into this plan
     int max_nb = 0, max_ldnb = 0, max_rank[3] = {0, 0, 0}, max_ldab = 0;

@@ -366,12 +366,17 @@ tfmm_status tfmm_plan_tuning_get(const tfmm_plan* plan, tfmm_tuning* t) {
 tfmm_status tfmm_plan_tuning_set(tfmm_plan* plan, const tfmm_tuning* t, void* stream) {
     return guarded([&] {
         TFMM_REQUIRE(plan && t, "null argument");
-        TFMM_REQUIRE(t->mrhs_precision == 0 || t->mrhs_precision == 2 || t->mrhs_precision == 3,
-                     "mrhs_precision must be 0, 2 or 3");
+        TFMM_REQUIRE(t->mrhs_precision >= 0 && t->mrhs_precision <= 3, "mrhs_precision must be 0, 1, 2 or 3");
         HotTuning h;
         h.agg_threads = t->agg_threads; h.agg_ctas_per_sm = t->agg_ctas_per_sm; h.agg_order = t->agg_order;
         h.dis_threads = t->dis_threads; h.dis_ctas_per_sm = t->dis_ctas_per_sm; h.dis_order = t->dis_order;
+        const HotTuning old = plan->p.tuning;
+        const bool was_ok = plan->p.hot_ok;
         configure_hot(plan->p, h, (cudaStream_t)stream);
+        if (was_ok && !plan->p.hot_ok) {
+            configure_hot(plan->p, old, (cudaStream_t)stream);
+            fail(TFMM_INVALID_ARG, "launch shape leaves no room for the largest work item");
+        }
         plan->p.params.mrhs_precision = t->mrhs_precision;
     });
 }
@@ -405,7 +410,7 @@ tfmm_status tfmm_autotune(tfmm_plan* plan, int32_t R, double budget_ms, int32_t 
         Timer tm;
         auto agg = [&] { run_stages(plan, 1, x, R, P.N, sp, 1, zero, y, P.N, s); };
         auto dis = [&] { run_stages(plan, 2, x, R, P.N, sp, 1, zero, y, P.N, s); };
-        if (R == 1) {
+        if (R == 1 && P.hot_ok) {
             // launch shape x queue order, one stage at a time; the other stage keeps its setting
             HotTuning best = P.tuning;
             double best_ms[2] = {1e30, 1e30};
@@ -423,6 +428,7 @@ tfmm_status tfmm_autotune(tfmm_plan* plan, int32_t R, double budget_ms, int32_t 
                             (stage == 0 ? t.agg_ctas_per_sm : t.dis_ctas_per_sm) = c;
                             (stage == 0 ? t.agg_order : t.dis_order) = order;
                             configure_hot(P, t, s);
+                            if (!P.hot_ok) continue;
                             const Schedule& sc = stage == 0 ? P.agg_sched : P.dis_sched;
                             if (std::find(seen.begin(), seen.end(), std::make_pair(nt * 2 + order, sc.blocks)) !=
                                 seen.end())
@@ -438,9 +444,11 @@ tfmm_status tfmm_autotune(tfmm_plan* plan, int32_t R, double budget_ms, int32_t 
             configure_hot(P, best, s);
             P.tuned_ms[0] = best_ms[0];
             P.tuned_ms[1] = best_ms[1];
-        } else {
-            // the multi-RHS engine: FP32 CUDA-core chain, 3-term (and on request 2-term) split BF16
+        } else if (R > 1) {
+            // the multi-RHS engine: 3-term split-BF16 chain, FP32 CUDA-core chain, the single-RHS
+            // kernels column by column, and on request the 2-term split
             std::vector<int> cand = {3, 0};
+            if (P.hot_ok) cand.push_back(1);
             if (allow_two_term) cand.push_back(2);
             int best = P.params.mrhs_precision;
             double best_ms = 1e30, ba = 0, bd = 0;

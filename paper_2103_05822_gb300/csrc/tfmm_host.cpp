@@ -155,22 +155,47 @@ void check_params(const tfmm_params& p) {
     TFMM_REQUIRE(p.quad_order >= 1 && p.quad_order <= 10, "quad_order must be in 1..10");
     TFMM_REQUIRE(p.max_rhs >= 1, "max_rhs must be >= 1");
     TFMM_REQUIRE(p.batch_groups >= 0, "batch_groups must be >= 0");
-    TFMM_REQUIRE(p.mrhs_precision == 0 || p.mrhs_precision == 2 || p.mrhs_precision == 3,
-                 "mrhs_precision must be 0, 2 or 3");
+    TFMM_REQUIRE(p.mrhs_precision >= 0 && p.mrhs_precision <= 3, "mrhs_precision must be 0, 1, 2 or 3");
 }
 
-// R > 1 runs the grouped-GEMM chains; TFMM_MR=loop keeps the single-RHS kernels
-// looping over the columns instead (for comparisons).
-bool mr_loop_forced() {
-    const char* e = std::getenv("TFMM_MR");
-    return e && std::strcmp(e, "loop") == 0;
-}
+// The engine that applies one call with R columns:
+//   columns: the persistent single-RHS kernels, one column after the other (R = 1, or
+//            mrhs_precision 1, or TFMM_MR=loop);
+//   chain:   the grouped-GEMM chain on FP32 CUDA cores (mrhs_precision 0), also the
+//            fallback when a work item does not fit the single-RHS kernels;
+//   tc:      the split-BF16 tensor-core chain with `terms` terms (mrhs_precision 2, 3).
+enum class Engine { columns, chain, tc };
 
-// Split-BF16 terms of the tensor-core chain for this call (0: FP32 CUDA-core chain).
-int tc_terms_for(const Plan& P, int R) {
-    if (R <= 1 || mr_loop_forced()) return 0;
+Engine engine_for(const Plan& P, int R, int* terms) {
+    *terms = 0;
     const int p = P.params.mrhs_precision;
-    return (p == 2 || p == 3) ? p : 0;
+    const char* e = std::getenv("TFMM_MR");
+    const bool loop = e && std::strcmp(e, "loop") == 0;
+    if (P.hot_ok && (R <= 1 || loop || p == 1)) return Engine::columns;
+    if (R > 1 && (p == 2 || p == 3)) {
+        *terms = p;
+        return Engine::tc;
+    }
+    return Engine::chain;
+}
+
+void run_aggregate(Plan& P, const float2* x, int R, int64_t ldx, float2* spec, cudaStream_t s) {
+    int T = 0;
+    switch (engine_for(P, R, &T)) {
+        case Engine::tc: launch_tc_aggregate(P, T, x, R, ldx, spec, s); break;
+        case Engine::chain: launch_mr_aggregate(P, x, R, ldx, spec, s); break;
+        default: launch_tucker_aggregate(P, x, R, ldx, spec, s);
+    }
+}
+
+void run_disaggregate(Plan& P, const float2* spec, int R, int weights, float2 beta, float2* y, int64_t ldy,
+                      cudaStream_t s) {
+    int T = 0;
+    switch (engine_for(P, R, &T)) {
+        case Engine::tc: launch_tc_disaggregate(P, T, spec, R, weights, beta, y, ldy, s); break;
+        case Engine::chain: launch_mr_disaggregate(P, spec, R, weights, beta, y, ldy, s); break;
+        default: launch_tucker_disaggregate(P, spec, R, weights, beta, y, ldy, s);
+    }
 }
 
 void check_hot(const Plan& P, const void* a, const void* b, int R, int64_t ld) {
@@ -422,7 +447,7 @@ tfmm_status tfmm_plan_info_get(const tfmm_plan* plan, tfmm_plan_info* info) {
 tfmm_status tfmm_plan_set_mrhs_precision(tfmm_plan* plan, int32_t precision) {
     return guarded([&] {
         TFMM_REQUIRE(plan, "null plan");
-        TFMM_REQUIRE(precision == 0 || precision == 2 || precision == 3, "mrhs_precision must be 0, 2 or 3");
+        TFMM_REQUIRE(precision >= 0 && precision <= 3, "mrhs_precision must be 0, 1, 2 or 3");
         plan->p.params.mrhs_precision = precision;
     });
 }
@@ -506,15 +531,8 @@ tfmm_status tfmm_aggregate(tfmm_plan* plan, const tfmm_cfloat* x, int32_t R, int
     return guarded([&] {
         TFMM_REQUIRE(plan, "null plan");
         check_hot(plan->p, x, spectra, R, ldx);
-        if (const int T = tc_terms_for(plan->p, R))
-            launch_tc_aggregate(plan->p, T, reinterpret_cast<const float2*>(x), R, ldx,
-                                reinterpret_cast<float2*>(spectra), (cudaStream_t)stream);
-        else if (R > 1 && !mr_loop_forced())
-            launch_mr_aggregate(plan->p, reinterpret_cast<const float2*>(x), R, ldx,
-                                reinterpret_cast<float2*>(spectra), (cudaStream_t)stream);
-        else
-            launch_tucker_aggregate(plan->p, reinterpret_cast<const float2*>(x), R, ldx,
-                                    reinterpret_cast<float2*>(spectra), (cudaStream_t)stream);
+        run_aggregate(plan->p, reinterpret_cast<const float2*>(x), R, ldx, reinterpret_cast<float2*>(spectra),
+                      (cudaStream_t)stream);
     });
 }
 
@@ -523,18 +541,8 @@ tfmm_status tfmm_disaggregate(tfmm_plan* plan, const tfmm_cfloat* spectra, int32
     return guarded([&] {
         TFMM_REQUIRE(plan, "null plan");
         check_hot(plan->p, spectra, y, R, ldy);
-        if (const int T = tc_terms_for(plan->p, R))
-            launch_tc_disaggregate(plan->p, T, reinterpret_cast<const float2*>(spectra), R, apply_weights,
-                                   make_float2(beta.re, beta.im), reinterpret_cast<float2*>(y), ldy,
-                                   (cudaStream_t)stream);
-        else if (R > 1 && !mr_loop_forced())
-            launch_mr_disaggregate(plan->p, reinterpret_cast<const float2*>(spectra), R, apply_weights,
-                                   make_float2(beta.re, beta.im), reinterpret_cast<float2*>(y), ldy,
-                                   (cudaStream_t)stream);
-        else
-            launch_tucker_disaggregate(plan->p, reinterpret_cast<const float2*>(spectra), R, apply_weights,
-                                       make_float2(beta.re, beta.im), reinterpret_cast<float2*>(y), ldy,
-                                       (cudaStream_t)stream);
+        run_disaggregate(plan->p, reinterpret_cast<const float2*>(spectra), R, apply_weights,
+                         make_float2(beta.re, beta.im), reinterpret_cast<float2*>(y), ldy, (cudaStream_t)stream);
     });
 }
 
@@ -583,15 +591,9 @@ tfmm_status tfmm_matvec_host(tfmm_plan* plan, const tfmm_cfloat* x_host, tfmm_cf
         if (dense) {
             launch_dense_aggregate(P, P.d_ws_x, R, P.N, P.d_ws_spec, s);
             launch_dense_disaggregate(P, P.d_ws_spec, R, 1, zero, P.d_ws_y, P.N, s);
-        } else if (const int T = tc_terms_for(P, R)) {
-            launch_tc_aggregate(P, T, P.d_ws_x, R, P.N, P.d_ws_spec, s);
-            launch_tc_disaggregate(P, T, P.d_ws_spec, R, 1, zero, P.d_ws_y, P.N, s);
-        } else if (R > 1 && !mr_loop_forced()) {
-            launch_mr_aggregate(P, P.d_ws_x, R, P.N, P.d_ws_spec, s);
-            launch_mr_disaggregate(P, P.d_ws_spec, R, 1, zero, P.d_ws_y, P.N, s);
         } else {
-            launch_tucker_aggregate(P, P.d_ws_x, R, P.N, P.d_ws_spec, s);
-            launch_tucker_disaggregate(P, P.d_ws_spec, R, 1, zero, P.d_ws_y, P.N, s);
+            run_aggregate(P, P.d_ws_x, R, P.N, P.d_ws_spec, s);
+            run_disaggregate(P, P.d_ws_spec, R, 1, zero, P.d_ws_y, P.N, s);
         }
         TFMM_CUDA_CHECK(cudaMemcpyAsync(y_host, P.d_ws_y, sizeof(float2) * P.N * R, cudaMemcpyDeviceToHost, s));
         TFMM_CUDA_CHECK(cudaStreamSynchronize(s));

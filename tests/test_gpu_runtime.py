@@ -209,7 +209,7 @@ def test_every_launch_shape_matches_oracle(synth, threads, ctas, order):
 def test_tuning_rejects_bad_shapes(synth):
     tfmm = _tfmm()
     for bad in ({"agg_threads": 1024}, {"dis_threads": 100}, {"agg_order": 2}, {"dis_ctas_per_sm": -1},
-                {"mrhs_precision": 1}):
+                {"mrhs_precision": 4}, {"mrhs_precision": -1}):
         with pytest.raises(tfmm.TfmmError) as e:
             tfmm.tfmm_plan_tuning_set(synth["plan"], **bad)
         assert e.value.status == tfmm.INVALID_ARG
@@ -222,7 +222,7 @@ def test_autotuner_choice_matches_oracle(synth, R):
     t = tfmm.tfmm_autotune(plan, R=R, budget_ms=3000.0)
     assert t["agg_ms"] > 0 and t["dis_ms"] > 0
     if R > 1:
-        assert t["mrhs_precision"] in (0, 3)
+        assert t["mrhs_precision"] in (0, 1, 3)
     G, nd, n = len(synth["members"]), synth["nt"] * synth["npf"], synth["n_rwg"]
     X = complex_gaussian((R, n), 80)
     x = torch.from_numpy(X.astype(np.complex64)).cuda()
@@ -232,3 +232,53 @@ def test_autotuner_choice_matches_oracle(synth, R):
     for r in range(R):
         ref = apply.aggregate_all(synth["T"], synth["members"], X[r])
         assert _rel(spec.cpu().numpy()[r], ref) <= 1e-5
+
+
+def test_column_engine_matches_oracle(synth):
+    """mrhs_precision 1: the single-RHS kernels, one column after another."""
+    tfmm = _tfmm()
+    plan = synth["plan"]
+    tfmm.tfmm_plan_set_mrhs_precision(plan, 1)
+    R, G, nd, n = 3, len(synth["members"]), synth["nt"] * synth["npf"], synth["n_rwg"]
+    X = complex_gaussian((R, n), 90)
+    gv = complex_gaussian((R, G, 2, nd), 91)
+    spec = torch.empty((R, G, 2, nd), dtype=torch.complex64, device="cuda")
+    tfmm.tfmm_aggregate(plan, torch.from_numpy(X.astype(np.complex64)).cuda(), spec)
+    y = torch.zeros((R, n), dtype=torch.complex64, device="cuda")
+    tfmm.tfmm_disaggregate(plan, torch.from_numpy(gv.astype(np.complex64)).cuda(), y)
+    tfmm.tfmm_sync(plan)
+    for r in range(R):
+        assert _rel(spec.cpu().numpy()[r], apply.aggregate_all(synth["T"], synth["members"], X[r])) <= 1e-5
+        refy = apply.disaggregate_all(synth["T"], synth["members"], gv[r], n, synth["w"])
+        assert _rel(y.cpu().numpy()[r], refy) <= 1e-5
+    tfmm.tfmm_plan_set_mrhs_precision(plan, 0)
+
+
+def test_items_too_large_for_one_cta_fall_back_to_the_chain():
+    """A group with 30,000 RWGs does not fit the single-RHS kernels' shared memory:
+    every call (R = 1 included) then runs the grouped-GEMM chain, same results."""
+    tfmm = _tfmm()
+    nt, npf, nbetas = 6, 12, [30000, 40]
+    ranks = [[(3, 4, 5), (2, 3, 4)], [(4, 5, 6), (3, 3, 7)]]
+    syn = synthetic_tucker(nt, npf, nbetas, ranks, 33)
+    n_rwg = sum(nbetas)
+    perm = np.random.default_rng(34).permutation(n_rwg)
+    members = [np.sort(perm[:nbetas[0]]), np.sort(perm[nbetas[0]:])]
+    T = [[hosvd.Tucker(s.U_theta, s.U_phi, s.U_beta, s.core) for s in per] for per in syn]
+    factors = [[(t.U_theta, t.U_phi, t.U_beta, t.core) for t in per] for per in T]
+    w = np.random.default_rng(35).uniform(0.05, 1.0, nt * npf)
+    plan = tfmm.tfmm_plan_from_tucker(n_rwg, nt, npf, members, factors, weights=w, max_rhs=2)
+    t = tfmm.tfmm_plan_tuning_get(plan)
+    assert t["agg_blocks"] == 0 or t["dis_blocks"] == 0
+    for R in (1, 2):
+        X = complex_gaussian((R, n_rwg), 36 + R)
+        gv = complex_gaussian((R, 2, 2, nt * npf), 38 + R)
+        spec = torch.empty((R, 2, 2, nt * npf), dtype=torch.complex64, device="cuda")
+        xd = torch.from_numpy(X.astype(np.complex64)).cuda()
+        tfmm.tfmm_aggregate(plan, xd if R > 1 else xd[0], spec)
+        y = torch.zeros((R, n_rwg), dtype=torch.complex64, device="cuda")
+        tfmm.tfmm_disaggregate(plan, torch.from_numpy(gv.astype(np.complex64)).cuda(), y if R > 1 else y[0])
+        tfmm.tfmm_sync(plan)
+        for r in range(R):
+            assert _rel(spec.cpu().numpy()[r], apply.aggregate_all(T, members, X[r])) <= 1e-5
+            assert _rel(y.cpu().numpy()[r], apply.disaggregate_all(T, members, gv[r], n_rwg, w)) <= 1e-5
