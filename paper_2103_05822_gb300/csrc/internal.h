@@ -155,6 +155,11 @@ struct TcPlan {             // per (R, terms): problem lists of the 8 steps and 
     FusedShape f34;
     DeviceBuffer f34_items, f34_tiles;
     int f34_ntiles = 0;
+    // DG1a with (i_phi, r) pairs as the MMA N dimension
+    bool dg1a = false;
+    int dg1a_K = 0, dg1a_NP = 0, dg1a_AR = 0, dg1a_ntiles = 0;
+    size_t dg1a_smem = 0;
+    DeviceBuffer dg1a_items, dg1a_tiles;
     ~TcPlan();
 };
 

@@ -343,10 +343,14 @@ __global__ void __launch_bounds__(TTHREADS) tc_gemm_kernel(const TcCtx c, const 
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t base = smem_u32(smem + b * STAGE);
             constexpr int PI[6] = {0, 0, 1, 0, 1, 2}, PJ[6] = {0, 1, 0, 2, 1, 0};
+            // K steps of 16 that hold data in this k-tile (the zero tail past K is skipped)
+            const int kseg = kt >= kt0 ? p.K1 : p.K0, koff = (kt >= kt0 ? kt - kt0 : kt) * TBK;
+            const int nsteps = min(2, (kseg - koff + 15) / 16);
 #pragma unroll
             for (int s16 = 0; s16 < 2; ++s16)
 #pragma unroll
                 for (int q = 0; q < n_products<T>(); ++q) {
+                    if (s16 >= nsteps) break;
                     const uint32_t ar = base + PI[q] * PLANE_TILE + s16 * 256;
                     const uint32_t ai = base + (T + PI[q]) * PLANE_TILE + s16 * 256;
                     const uint32_t br = base + (2 * T + PJ[q]) * PLANE_TILE + s16 * 256;
@@ -695,6 +699,164 @@ __global__ void __launch_bounds__(F34_THREADS) tc_ag34_kernel(const TcCtx c, con
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(sh.tcols));
 }
 
+// ------------------------------------------------- DG1a with (i_phi, r) as N
+// P'_r[i_phi][a] = sum_theta conj(W g_r)[theta][i_phi] U_theta[theta][a] (Fig. 3b
+// step 1, first factor) as D[a][(i_phi, r)]: U_theta^T is the A operand (the r_theta
+// rows on the TMEM lanes), NP (i_phi, r) pairs of the weighted, conjugated FP32
+// spectra are the B operand, split in registers.  One MMA then covers NP = 128 (or
+// 64) pairs instead of r_theta columns.  The result goes TMEM -> shared memory ->
+// the P'' planes [a + r_t r][i_phi] that DG1b reads.
+struct D1Item {
+    const bf16* uth; int64_t uth_ld, uth_ps;  // U_theta planes [a][i_theta]
+    bf16* out; int64_t o_ld, o_ps;            // P'' planes [a + r_t r][i_phi]
+    int g, alpha, rt;
+};
+struct D1Tile { int item, p0; };
+
+constexpr int D1_THREADS = 256;
+
+template <int T>
+__global__ void __launch_bounds__(D1_THREADS) tc_dg1a_kernel(const TcCtx c, const D1Item* __restrict__ items,
+                                                            const D1Tile* __restrict__ tiles, int K, int NP,
+                                                            int AR, int tcols, int n_phi) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const D1Tile t = tiles[blockIdx.x];
+    const D1Item it = items[t.item];
+    const int nt = c.n_theta, npairs = n_phi * c.R;
+    // A planes hold AR >= r_theta rows; the MMA reads 128 rows per plane, the rows past AR
+    // (data of the next plane or of B, inside this CTA's shared memory) only reach lanes
+    // past r_theta, which are never read back
+    const int ap = AR * K * 2, bp = NP * K * 2;
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + 2 * T * ap;
+    float2* stage = reinterpret_cast<float2*>(sB);  // reused once the MMAs are done
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(tcols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    // A: U_theta^T, r_theta rows (lanes past r_theta hold no output)
+    load_planes<T>(sA, ap, K, it.uth, it.uth_ld, it.uth_ps, it.rt, it.rt, nt);
+    asm volatile("cp.async.commit_group;");
+    // B: pair row p0 + i = i_phi + n_phi r, depth theta; conj(W g), zero past n_theta and n_phi R.
+    // Every load of a thread is issued before the splits (memory-level parallelism).
+    const int kc8 = K / 8, ntask = NP * kc8;
+    constexpr int ITER = 4;  // NP * K / 8 <= 4 * D1_THREADS (host check)
+    float2 v[ITER][8];
+#pragma unroll
+    for (int u = 0; u < ITER; ++u) {
+        const int task = tid + u * D1_THREADS, i = task / kc8, kc = task % kc8, p = t.p0 + i;
+        const bool row_ok = task < ntask && p < npairs;
+        const int ip = row_ok ? p % n_phi : 0, r = row_ok ? p / n_phi : 0;
+        const int64_t o = (((int64_t)r * c.G + it.g) * 2 + it.alpha) * c.n_dir + (int64_t)nt * ip;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int th = kc * 8 + e;
+            v[u][e] = make_float2(0.f, 0.f);
+            if (row_ok && th < nt) {
+                const float2 g = __ldg(c.spec_in + o + th);
+                const float wt = c.w ? __ldg(c.w + th + (int64_t)nt * ip) : 1.0f;
+                v[u][e] = make_float2(wt * g.x, -wt * g.y);
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < ITER; ++u) {
+        const int task = tid + u * D1_THREADS, i = task / kc8, kc = task % kc8;
+        if (task >= ntask) break;
+        uint32_t w[2 * T][4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+            uint32_t r0[3], i0[3], r1[3], i1[3];
+            split_bits<T>(v[u][e].x, r0); split_bits<T>(v[u][e].y, i0);
+            split_bits<T>(v[u][e + 1].x, r1); split_bits<T>(v[u][e + 1].y, i1);
+#pragma unroll
+            for (int q = 0; q < T; ++q) {
+                w[q][e / 2] = pack_hi(r0[q], r1[q]);
+                w[T + q][e / 2] = pack_hi(i0[q], i1[q]);
+            }
+        }
+        const int off = (i >> 3) * (K * 16) + kc * 128 + (i & 7) * 16;
+#pragma unroll
+        for (int q = 0; q < 2 * T; ++q)
+            *reinterpret_cast<uint4*>(sB + q * bp + off) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+    }
+    asm volatile("cp.async.wait_group 0;");
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tm = tmem_base;
+    if (tid == 0) {
+        issue_products<T>(tm, tm + NP, smem_u32(sA), ap, smem_u32(sB), bp, K * 16, K * 16, K / 16, idesc_bf16(NP));
+        mma_commit(&mbar);
+    }
+    bool ok = mbar_wait(&mbar, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    ok = __syncthreads_and(ok);
+    if (ok) {
+        // D[a][pair] -> stage[a][pair] (the warps whose lane quarter holds some a < r_theta)
+        if (warp < 4 && warp * 32 < it.rt) {
+            const uint32_t lanes = (uint32_t)(warp * 32) << 16;
+            const int a = warp * 32 + lane;
+            for (int c0 = 0; c0 < NP; c0 += 32) {
+                uint32_t vr[32], vi[32];
+                tmem_ld32(vr, tm + lanes + c0);
+                tmem_ld32(vi, tm + lanes + NP + c0);
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+                if (a < it.rt) {
+#pragma unroll
+                    for (int e = 0; e < 32; ++e)
+                        stage[a * NP + c0 + e] = make_float2(__uint_as_float(vr[e]), __uint_as_float(vi[e]));
+                }
+            }
+        }
+        __syncthreads();
+        // stage -> P'' planes, row a + r_t r, column i_phi: eight pairs per task
+        for (int task = tid; task < it.rt * (NP / 8); task += D1_THREADS) {
+            const int a = task / (NP / 8), c8 = (task % (NP / 8)) * 8, p = t.p0 + c8;
+            if (p >= npairs) continue;
+            const int ip = p % n_phi, r = p / n_phi;
+            const bool vec = ip + 8 <= n_phi && (ip & 7) == 0 && (it.o_ld & 7) == 0 && p + 8 <= npairs;
+            if (vec) {
+                uint32_t w[2 * T][4];
+#pragma unroll
+                for (int e = 0; e < 8; e += 2) {
+                    const float2 x0 = stage[a * NP + c8 + e], x1 = stage[a * NP + c8 + e + 1];
+                    uint32_t r0[3], i0[3], r1[3], i1[3];
+                    split_bits<T>(x0.x, r0); split_bits<T>(x0.y, i0);
+                    split_bits<T>(x1.x, r1); split_bits<T>(x1.y, i1);
+#pragma unroll
+                    for (int q = 0; q < T; ++q) {
+                        w[q][e / 2] = pack_hi(r0[q], r1[q]);
+                        w[T + q][e / 2] = pack_hi(i0[q], i1[q]);
+                    }
+                }
+                bf16* dst = it.out + (int64_t)(a + it.rt * r) * it.o_ld + ip;
+#pragma unroll
+                for (int q = 0; q < 2 * T; ++q)
+                    *reinterpret_cast<uint4*>(dst + q * it.o_ps) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+            } else {
+                for (int e = 0; e < 8 && p + e < npairs; ++e) {
+                    const int pe = p + e, ipe = pe % n_phi, re = pe / n_phi;
+                    store_planes<T>(it.out, it.o_ps, (int64_t)(a + it.rt * re) * it.o_ld + ipe, stage[a * NP + c8 + e]);
+                }
+            }
+        }
+    } else {
+        mbar_wait(&mbar, 0);  // no MMA may still run when TMEM is freed
+        if (tid == 0) atomicAdd(c.err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(tcols));
+}
+
 // ------------------------------------------------------------ operand prep
 // Split planes of an FP32 complex matrix: dst[p][r][k] for r < rows, k < cols,
 // src element (r, k) at src[r * sr + k * sk]; entries k in [cols, ld) stay as they are.
@@ -979,6 +1141,70 @@ void launch_ag34(const Plan& P, const TcPlan& M, const TcCtx& c, cudaStream_t s)
     TFMM_CUDA_CHECK(cudaGetLastError());
 }
 
+// DG1a with the (i_phi, r) pairs as N: NP = 128 pairs per CTA when shared memory allows,
+// else 64; leaves M.dg1a false when neither fits (the generic stage kernel runs instead).
+template <class VOff>
+void plan_dg1a(const Plan& P, TcPlan& M, const bf16* F, const std::vector<TcItem>& tci, bf16* Vb, VOff voff) {
+    M.dg1a = false;
+    if (!fused_enabled()) return;
+    if (const char* e = std::getenv("TFMM_TC_DG1A"); e && e[0] == '0') return;
+    const int T = M.T, R = M.R, nt = P.n_theta, np = P.n_phi;
+    if (P.max_rank[0] > TBM) return;
+    const int K = (nt + 15) & ~15;
+    const int AR = (int)r8(P.max_rank[0]);
+    // 128 pairs per CTA (two CTAs per SM when shared memory allows), else 64; the staged
+    // result (r_theta x NP complex) reuses B, the loads are at most 4 tasks per thread
+    int NP = 0;
+    for (int cand : {128, 64}) {
+        const size_t smem = (size_t)2 * T * 2 * K * (AR + cand);
+        const bool stage_fits = (size_t)P.max_rank[0] * cand * 8 <= (size_t)2 * T * 2 * K * cand;
+        const bool overread_fits = (size_t)2 * T * cand >= TBM;  // B covers the A planes' rows past AR
+        const bool tasks_fit = cand * (K / 8) <= 4 * D1_THREADS;
+        if (smem <= kMaxDynSmem && stage_fits && overread_fits && tasks_fit) {
+            NP = cand;
+            break;
+        }
+    }
+    if (NP == 0) return;
+    std::vector<D1Item> items(P.items.size());
+    for (size_t q = 0; q < P.items.size(); ++q) {
+        const TuckerItem& d = P.items[q];
+        const TcMat& u = tci[q].uth;
+        D1Item& it = items[q];
+        it.uth = F + u.off; it.uth_ld = u.ld; it.uth_ps = (int64_t)u.rows * u.ld;
+        it.out = Vb + voff((int)q); it.o_ld = r8(np); it.o_ps = (int64_t)d.rt * R * r8(np);
+        it.g = d.g; it.alpha = d.alpha; it.rt = d.rt;
+    }
+    std::vector<D1Tile> tiles;
+    const int npairs = np * R;
+    for (size_t q = 0; q < P.items.size(); ++q)
+        for (int p0 = 0; p0 < npairs; p0 += NP) tiles.push_back(D1Tile{(int)q, p0});
+    TFMM_CUDA_CHECK(cudaMalloc(&M.dg1a_items.p, sizeof(D1Item) * items.size()));
+    TFMM_CUDA_CHECK(cudaMalloc(&M.dg1a_tiles.p, sizeof(D1Tile) * tiles.size()));
+    TFMM_CUDA_CHECK(cudaMemcpy(M.dg1a_items.p, items.data(), sizeof(D1Item) * items.size(), cudaMemcpyHostToDevice));
+    TFMM_CUDA_CHECK(cudaMemcpy(M.dg1a_tiles.p, tiles.data(), sizeof(D1Tile) * tiles.size(), cudaMemcpyHostToDevice));
+    M.dg1a_ntiles = (int)tiles.size();
+    M.dg1a_K = K;
+    M.dg1a_NP = NP;
+    M.dg1a_smem = (size_t)2 * T * 2 * K * (AR + NP);
+    M.dg1a_AR = AR;
+    M.dg1a = true;
+}
+
+template <int T>
+void launch_dg1a(const Plan& P, const TcPlan& M, const TcCtx& c, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        TFMM_CUDA_CHECK(cudaFuncSetAttribute(tc_dg1a_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kMaxDynSmem));
+        attr = true;
+    }
+    tc_dg1a_kernel<T><<<M.dg1a_ntiles, D1_THREADS, M.dg1a_smem, s>>>(
+        c, static_cast<const D1Item*>(M.dg1a_items.p), static_cast<const D1Tile*>(M.dg1a_tiles.p), M.dg1a_K,
+        M.dg1a_NP, M.dg1a_AR, 2 * M.dg1a_NP, P.n_phi);
+    TFMM_CUDA_CHECK(cudaGetLastError());
+}
+
 }  // namespace
 
 TcPlan* get_tc_plan(Plan& P, int R, int T, cudaStream_t s) {
@@ -1103,6 +1329,7 @@ TcPlan* get_tc_plan(Plan& P, int R, int T, cudaStream_t s) {
         upload_tc_stage(M.st[st], pr[st], tl[st]);
     }
     plan_fused34(P, M, F, tci, Mb, [&](int q) { return of[q].m; });
+    plan_dg1a(P, M, F, tci, Vb, [&](int q) { return of[q].v; });
     P.tc.push_back(std::move(tp));
     return P.tc.back().get();
 }
@@ -1145,7 +1372,10 @@ void tc_disaggregate_t(Plan& P, TcPlan& M, const float2* spec, int R, int weight
                                             R, P.G, P.n_theta, P.n_phi);
         TFMM_CUDA_CHECK(cudaGetLastError());
     }
-    launch_tc<T, TDG1A>(M.st[TDG1A], c, s);
+    if (M.dg1a)
+        launch_dg1a<T>(P, M, c, s);
+    else
+        launch_tc<T, TDG1A>(M.st[TDG1A], c, s);
     launch_tc<T, TDG1B>(M.st[TDG1B], c, s);
     launch_tc<T, TDG2>(M.st[TDG2], c, s);
     launch_tc<T, TDG3>(M.st[TDG3], c, s);
