@@ -74,6 +74,14 @@ __device__ __forceinline__ float2 warp_sum(float2 v) {
     return v;
 }
 
+// Starts pulling the head of an array that a later phase streams into L2, so that
+// DRAM stays busy through the short shared-memory phases before it (one thread).
+constexpr uint32_t kPrefetchBytes = 128 * 1024;
+__device__ __forceinline__ void prefetch_head_l2(const void* p, int64_t bytes) {
+    const uint32_t n = (uint32_t)(bytes < (int64_t)kPrefetchBytes ? bytes : (int64_t)kPrefetchBytes) & ~15u;
+    if (n) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(n) : "memory");
+}
+
 // Next work item of this CTA, or >= n_items when the queue is drained.  The
 // CTA that drains last resets the counters for the next launch.
 __device__ __forceinline__ int next_item(unsigned* ctr, unsigned* done, int n_items, int* s_item) {
@@ -196,6 +204,10 @@ __global__ void __launch_bounds__(512) tucker_aggregate_kernel(const AggArgs a) 
         const float2* Cc = a.fac + d.core;
         const float2* Up = a.fac + d.uphi;
         const float2* Ut = a.fac + d.uth;
+        if (tid == 0) {  // AG1 and AG2 stream these right after the staging below
+            prefetch_head_l2(Ub, (int64_t)d.rb * d.ld_nb * 8);
+            prefetch_head_l2(Cc, (int64_t)d.rb * d.ld_ab * 8);
+        }
         for (int r = 0; r < a.R; ++r) {
             // stage the small factors and the group's currents
             for (int e = tid; e < a.n_theta * d.rt; e += NT) s_ut[(e % a.n_theta) + a.L.ldt * (e / a.n_theta)] = Ut[e];
@@ -278,6 +290,10 @@ __global__ void __launch_bounds__(512) tucker_disaggregate_kernel(const DisArgs 
                 const float2* Up = a.fac + d.uphi;
                 const float2* Ut = a.fac + d.uth;
                 const float2* gin = a.spec + (((int64_t)r * a.G + g) * 2 + al) * a.n_dir;
+                if (tid == 0) {  // DG2 and DG3 stream these after the DG1 phase
+                    prefetch_head_l2(Cc, (int64_t)d.rb * d.ld_ab * 8);
+                    prefetch_head_l2(Ub, (int64_t)d.rb * d.ld_nb * 8);
+                }
                 for (int e = tid; e < a.n_theta * d.rt; e += NT) s_ut[(e % a.n_theta) + a.L.ldt * (e / a.n_theta)] = Ut[e];
                 for (int e = tid; e < a.n_phi * d.rp; e += NT) s_up[(e % a.n_phi) + a.L.ldp * (e / a.n_phi)] = Up[e];
                 for (int o = tid; o < a.n_dir; o += NT) {
@@ -307,6 +323,10 @@ __global__ void __launch_bounds__(512) tucker_disaggregate_kernel(const DisArgs 
                 rowdot<false>(reinterpret_cast<const float4*>(Cc), d.ld_ab / 2, d.rb,
                               reinterpret_cast<const float4*>(s_H), [&](int c, float2 v) { s_s[c] = v; });
                 __syncthreads();
+                if (tid == 0 && al == 0) {  // the next component's C while this one's U_beta streams
+                    const TuckerItem d1 = a.items[2 * g + 1];
+                    prefetch_head_l2(a.fac + d1.core, (int64_t)d1.rb * d1.ld_ab * 8);
+                }
                 // DG3: y_n += conj(sum_c U_beta[n, c] s[c])
                 rowaxpy(reinterpret_cast<const float4*>(Ub), d.ld_nb / 2, d.rb, s_s, s_part, [&](int j, float4 v) {
                     float4 o = s_y4[j];
