@@ -210,4 +210,6 @@ WORKLOADS = {
     "sphere30": Workload("sphere30", 30.0, 180, 2.0, 6, 1e-6, 1, "gaussian", 3),
     "sphere30_rcs128": Workload("sphere30_rcs128", 30.0, 180, 2.0, 6, 1e-6, 128, "planewave_sweep", 4),
     "sphere20_sweep": Workload("sphere20_sweep", 20.0, 120, 2.0, 6, 1e-6, 16, "gaussian", 5),
+    # the 10-lambda sphere with 128 CN(0,1) RHS: a small case of the many-RHS path (profiling)
+    "sphere10_rhs128": Workload("sphere10_rhs128", 10.0, 60, 1.0, 6, 1e-6, 128, "gaussian", 6),
 }
