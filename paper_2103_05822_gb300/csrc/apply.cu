@@ -262,7 +262,7 @@ struct DisArgs {
 };
 
 // Disaggregation (Fig. 3b) of one group (both alpha) per work item.
-__global__ void __launch_bounds__(512) tucker_disaggregate_kernel(const DisArgs a) {
+__global__ void __launch_bounds__(512, 3) tucker_disaggregate_kernel(const DisArgs a) {
     extern __shared__ float4 smem4[];
     float2* sm = reinterpret_cast<float2*>(smem4);
     __shared__ int s_item;
