@@ -67,6 +67,21 @@ def dist_env():
     return world, rank, local
 
 
+def whole_job_ms(total_ms, steps, world, device=None):
+    """The slowest replica's timed total (max over ranks) and the whole job's ms per matvec.
+
+    Replicas run side by side, one per GPU, each doing one matvec per step, so the job
+    finishes steps * world matvecs in the slowest rank's time.
+    """
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, total_ms / (steps * world)
+
+
 def workload_desc(w, L=None, n_theta=None, n_phi=None, G=None):
     d = (f"PEC sphere D={w.diameter:g} lambda, icosphere nu={w.nu} ({w.n_tri} triangles, {w.n_rwg} RWGs), "
          f"{w.box:g}-lambda boxes, d0={w.digits} digits")
@@ -364,12 +379,7 @@ def run_ours(args, w, world, rank, local):
     ms_step = total / args.steps
     if graph is not None:  # per-stage split from an eager pass
         _, agg, dis = timed(step_tucker, args.steps, args.warmup)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
-    value = total / (args.steps * world)  # whole-job ms per matvec (replicas run side by side)
+    total, value = whole_job_ms(total, args.steps, world, dev)
 
     dense = None
     if use_dense:
