@@ -37,7 +37,10 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstdlib>
+#include <mutex>
 #include <numeric>
+#include <set>
+#include <utility>
 #include <vector>
 
 #include "internal.h"
@@ -919,6 +922,19 @@ bool tc_split_accumulators() {
     return on;
 }
 
+// Raises a kernel's dynamic shared-memory limit, once per (device, kernel): the
+// attribute belongs to the current device's context.
+void allow_dyn_smem(const void* kernel, size_t bytes) {
+    static std::mutex mu;
+    static std::set<std::pair<int, const void*>> done;
+    int dev = 0;
+    TFMM_CUDA_CHECK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({dev, kernel})) return;
+    TFMM_CUDA_CHECK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    done.insert({dev, kernel});
+}
+
 // Ring depth and TMEM columns from the stage's largest K and BN; shared memory is
 // padded so that the CTAs one SM can hold never ask for more than its 512 columns.
 template <int T, int S>
@@ -936,12 +952,7 @@ void launch_tc(const TcStagePlan& st, const TcCtx& c, cudaStream_t s) {
     constexpr size_t kSmemSM = 228 * 1024, kMaxDyn = 225 * 1024;
     size_t smem = nst * STAGE;
     if (kSmemSM / (smem + 2048) > (size_t)ctas_tmem) smem = std::min(kMaxDyn, kSmemSM / ctas_tmem - 2048);
-    static bool attr = false;
-    if (!attr) {
-        TFMM_CUDA_CHECK(cudaFuncSetAttribute(tc_gemm_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kMaxDyn));
-        attr = true;
-    }
+    allow_dyn_smem(reinterpret_cast<const void*>(tc_gemm_kernel<T, S>), kMaxDyn);
     tc_gemm_kernel<T, S><<<st.n_tiles, TTHREADS, smem, s>>>(c, reinterpret_cast<const TcProb*>(st.d_probs), st.d_tiles,
                                                              nst, tcols, cofs, hsplit);
     TFMM_CUDA_CHECK(cudaGetLastError());
@@ -1130,12 +1141,7 @@ void plan_fused34(const Plan& P, TcPlan& M, const bf16* F, const std::vector<TcI
 
 template <int T>
 void launch_ag34(const Plan& P, const TcPlan& M, const TcCtx& c, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        TFMM_CUDA_CHECK(cudaFuncSetAttribute(tc_ag34_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kMaxDynSmem));
-        attr = true;
-    }
+    allow_dyn_smem(reinterpret_cast<const void*>(tc_ag34_kernel<T>), kMaxDynSmem);
     tc_ag34_kernel<T><<<M.f34_ntiles, F34_THREADS, M.f34.smem, s>>>(
         c, static_cast<const F34Item*>(M.f34_items.p), static_cast<const F34Tile*>(M.f34_tiles.p), M.f34, P.n_phi);
     TFMM_CUDA_CHECK(cudaGetLastError());
@@ -1193,12 +1199,7 @@ void plan_dg1a(const Plan& P, TcPlan& M, const bf16* F, const std::vector<TcItem
 
 template <int T>
 void launch_dg1a(const Plan& P, const TcPlan& M, const TcCtx& c, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        TFMM_CUDA_CHECK(cudaFuncSetAttribute(tc_dg1a_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kMaxDynSmem));
-        attr = true;
-    }
+    allow_dyn_smem(reinterpret_cast<const void*>(tc_dg1a_kernel<T>), kMaxDynSmem);
     tc_dg1a_kernel<T><<<M.dg1a_ntiles, D1_THREADS, M.dg1a_smem, s>>>(
         c, static_cast<const D1Item*>(M.dg1a_items.p), static_cast<const D1Tile*>(M.dg1a_tiles.p), M.dg1a_K,
         M.dg1a_NP, M.dg1a_AR, 2 * M.dg1a_NP, P.n_phi);
