@@ -297,13 +297,19 @@ tfmm_status tfmm_graph_destroy(tfmm_graph* graph);
  * 32), CTAs per SM (0 = as many as fit) and the work-queue order (0 = most
  * factor bytes first, 1 = group order) of the persistent aggregation and
  * disaggregation kernels.  R > 1: the engine (mrhs_precision as in
- * tfmm_params). */
+ * tfmm_params) and two tile shapes of the tensor-core chain.  Changing the
+ * tile shapes rebuilds the chains' tile lists (INVALID_ARG while captured
+ * graphs of the plan exist). */
 typedef struct {
     int32_t agg_threads, agg_ctas_per_sm, agg_order;
     int32_t dis_threads, dis_ctas_per_sm, dis_order;
     int32_t agg_blocks, dis_blocks; /* resulting persistent grids (ignored by _set) */
     int32_t mrhs_precision;
-    int32_t reserved[3];
+    int32_t tc_f34_n1;              /* tensor cores: cap on r_theta x RHS per CTA of the fused
+                                       AG3+AG4 kernel, 0 or 16..256 (0: the largest that fits) */
+    int32_t tc_dg1a_pairs;          /* tensor cores: (i_phi, r) pairs per CTA of DG1a, 0, 64 or 128
+                                       (0: 128 when it fits, else 64) */
+    int32_t reserved[1];
     double agg_ms, dis_ms;          /* times the autotuner measured (0 if not tuned) */
 } tfmm_tuning;
 tfmm_status tfmm_plan_tuning_get(const tfmm_plan* plan, tfmm_tuning* t);
@@ -314,7 +320,8 @@ tfmm_status tfmm_plan_tuning_set(tfmm_plan* plan, const tfmm_tuning* t, void* st
  * fastest.  R == 1 searches launch shape and queue order of each stage; R > 1
  * chooses the engine among the 3-term tensor-core chain, the FP32 CUDA-core
  * chain and the single-RHS kernels column by column (and the 2-term chain
- * when allow_two_term != 0, which is less accurate).  The search stops early
+ * when allow_two_term != 0, which is less accurate), then, for a tensor-core
+ * engine, the two tile shapes of tfmm_tuning.  The search stops early
  * once budget_ms of wall time is spent.  `out` (may be NULL) receives the
  * chosen tuning.  No counterpart in the paper. */
 tfmm_status tfmm_autotune(tfmm_plan* plan, int32_t R, double budget_ms, int32_t allow_two_term, void* stream,

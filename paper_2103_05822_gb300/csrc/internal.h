@@ -160,6 +160,8 @@ struct TcPlan {             // per (R, terms): problem lists of the 8 steps and 
     int dg1a_K = 0, dg1a_NP = 0, dg1a_AR = 0, dg1a_ntiles = 0;
     size_t dg1a_smem = 0;
     DeviceBuffer dg1a_items, dg1a_tiles;
+    // per item: element offsets of its M' and V'' / P'' scratch planes (for re-planning)
+    std::vector<int64_t> m_off, v_off;
     ~TcPlan();
 };
 
@@ -214,6 +216,8 @@ struct Plan {
     std::vector<TuckerItem> items;
     Schedule agg_sched, dis_sched;
     HotTuning tuning;
+    int tc_f34_n1 = 0;                 // cap on r_theta x RHS per CTA of the fused AG3+AG4 kernel (0: largest that fits)
+    int tc_dg1a_pairs = 0;             // (i_phi, r) pairs per CTA of the DG1a kernel (0: 128 when it fits, else 64)
     bool hot_ok = false;               // the single-RHS kernels fit (shared memory of the largest item)
     double tuned_ms[2] = {0, 0};       // autotuner's best aggregate / disaggregate times
     int live_graphs = 0;               // captured graphs that still point into this plan
@@ -288,6 +292,7 @@ void configure_hot(Plan& P, const HotTuning& t, cudaStream_t s);  // orders and 
 // mrhs_tc.cu
 void build_tc_factors(Plan& P, int T, cudaStream_t s);
 TcPlan* get_tc_plan(Plan& P, int R, int T, cudaStream_t s);
+void tc_replan_shapes(Plan& P);  // re-plans the fused AG3+AG4 and DG1a kernels of every chain after a preference change
 void launch_tc_aggregate(Plan& P, int T, const float2* x, int R, int64_t ldx, float2* spec, cudaStream_t s);
 void launch_tc_disaggregate(Plan& P, int T, const float2* spec, int R, int weights, float2 beta, float2* y,
                             int64_t ldy, cudaStream_t s);

@@ -1095,6 +1095,7 @@ void plan_fused34(const Plan& P, TcPlan& M, const bf16* F, const std::vector<TcI
     const int n1s_cap = ((512 - f.nbuf * 2 * f.nacc * f.ntp) / 2) & ~31;
     int n1max = std::min(256, n1s_cap);
     if (const char* e = std::getenv("TFMM_TC_F34_N1")) n1max = std::min(n1max, std::max(16, std::atoi(e)) & ~15);
+    if (P.tc_f34_n1 > 0) n1max = std::min(n1max, std::max(16, P.tc_f34_n1) & ~15);
     while (n1max >= 16 && f34_smem(T, f.K1, f.K2, n1max, f.ntp, nt, np) > kMaxDynSmem) n1max -= 16;
     if (n1max < ((P.max_rank[0] + 15) & ~15)) return;
     std::vector<F34Item> items(P.items.size());
@@ -1162,6 +1163,7 @@ void plan_dg1a(const Plan& P, TcPlan& M, const bf16* F, const std::vector<TcItem
     // result (r_theta x NP complex) reuses B, the loads are at most 4 tasks per thread
     int NP = 0;
     for (int cand : {128, 64}) {
+        if (P.tc_dg1a_pairs > 0 && cand != P.tc_dg1a_pairs) continue;
         const size_t smem = (size_t)2 * T * 2 * K * (AR + cand);
         const bool stage_fits = (size_t)P.max_rank[0] * cand * 8 <= (size_t)2 * T * 2 * K * cand;
         const bool overread_fits = (size_t)2 * T * cand >= TBM;  // B covers the A planes' rows past AR
@@ -1329,10 +1331,34 @@ TcPlan* get_tc_plan(Plan& P, int R, int T, cudaStream_t s) {
     for (int st = 0; st < 8; ++st) {
         upload_tc_stage(M.st[st], pr[st], tl[st]);
     }
-    plan_fused34(P, M, F, tci, Mb, [&](int q) { return of[q].m; });
-    plan_dg1a(P, M, F, tci, Vb, [&](int q) { return of[q].v; });
+    M.m_off.resize(nI);
+    M.v_off.resize(nI);
+    for (int q = 0; q < nI; ++q) {
+        M.m_off[q] = of[q].m;
+        M.v_off[q] = of[q].v;
+    }
+    plan_fused34(P, M, F, tci, Mb, [&](int q) { return M.m_off[q]; });
+    plan_dg1a(P, M, F, tci, Vb, [&](int q) { return M.v_off[q]; });
     P.tc.push_back(std::move(tp));
     return P.tc.back().get();
+}
+
+void tc_replan_shapes(Plan& P) {
+    TFMM_REQUIRE(P.live_graphs == 0, "captured graphs use the current tile lists: destroy them first");
+    TFMM_CUDA_CHECK(cudaDeviceSynchronize());  // no launch may still read the old lists
+    for (auto& mp : P.tc) {
+        TcPlan& M = *mp;
+        for (DeviceBuffer* b : {&M.f34_items, &M.f34_tiles, &M.dg1a_items, &M.dg1a_tiles}) {
+            if (b->p) cudaFree(b->p);
+            b->p = nullptr;
+        }
+        const bf16* F = reinterpret_cast<const bf16*>(P.tc_fac[M.T].p);
+        const std::vector<TcItem>& tci = P.tc_items[M.T];
+        bf16* Mb = reinterpret_cast<bf16*>(M.buf[2]);
+        bf16* Vb = reinterpret_cast<bf16*>(M.buf[3]);
+        plan_fused34(P, M, F, tci, Mb, [&](int q) { return M.m_off[q]; });
+        plan_dg1a(P, M, F, tci, Vb, [&](int q) { return M.v_off[q]; });
+    }
 }
 
 namespace {

@@ -358,6 +358,8 @@ tfmm_status tfmm_plan_tuning_get(const tfmm_plan* plan, tfmm_tuning* t) {
         t->agg_blocks = P.agg_sched.blocks;
         t->dis_blocks = P.dis_sched.blocks;
         t->mrhs_precision = P.params.mrhs_precision;
+        t->tc_f34_n1 = P.tc_f34_n1;
+        t->tc_dg1a_pairs = P.tc_dg1a_pairs;
         t->agg_ms = P.tuned_ms[0];
         t->dis_ms = P.tuned_ms[1];
     });
@@ -367,6 +369,16 @@ tfmm_status tfmm_plan_tuning_set(tfmm_plan* plan, const tfmm_tuning* t, void* st
     return guarded([&] {
         TFMM_REQUIRE(plan && t, "null argument");
         TFMM_REQUIRE(t->mrhs_precision >= 0 && t->mrhs_precision <= 3, "mrhs_precision must be 0, 1, 2 or 3");
+        TFMM_REQUIRE(t->tc_f34_n1 == 0 || (t->tc_f34_n1 >= 16 && t->tc_f34_n1 <= 256 && t->tc_f34_n1 % 16 == 0),
+                     "tc_f34_n1 must be 0 or a multiple of 16 in 16..256");
+        TFMM_REQUIRE(t->tc_dg1a_pairs == 0 || t->tc_dg1a_pairs == 64 || t->tc_dg1a_pairs == 128,
+                     "tc_dg1a_pairs must be 0, 64 or 128");
+        if (t->tc_f34_n1 != plan->p.tc_f34_n1 || t->tc_dg1a_pairs != plan->p.tc_dg1a_pairs) {
+            TFMM_REQUIRE(plan->p.live_graphs == 0, "destroy the plan's graphs before changing tile shapes");
+            plan->p.tc_f34_n1 = t->tc_f34_n1;
+            plan->p.tc_dg1a_pairs = t->tc_dg1a_pairs;
+            tc_replan_shapes(plan->p);
+        }
         HotTuning h;
         h.agg_threads = t->agg_threads; h.agg_ctas_per_sm = t->agg_ctas_per_sm; h.agg_order = t->agg_order;
         h.dis_threads = t->dis_threads; h.dis_ctas_per_sm = t->dis_ctas_per_sm; h.dis_order = t->dis_order;
@@ -467,6 +479,32 @@ tfmm_status tfmm_autotune(tfmm_plan* plan, int32_t R, double budget_ms, int32_t 
             P.params.mrhs_precision = best;
             P.tuned_ms[0] = ba;
             P.tuned_ms[1] = bd;
+            if ((best == 2 || best == 3) && P.live_graphs == 0) {
+                // tile shapes of the tensor-core chain: fused AG3+AG4 block size x DG1a pairs
+                int bn1 = P.tc_f34_n1, bpairs = P.tc_dg1a_pairs;
+                for (int n1 : {0, 128, 64})
+                    for (int pairs : {0, 64}) {
+                        if (spent() > budget_ms) break;
+                        if (n1 == bn1 && pairs == bpairs) continue;
+                        P.tc_f34_n1 = n1;
+                        P.tc_dg1a_pairs = pairs;
+                        tc_replan_shapes(P);
+                        const double a = time_ms(agg, 2, s, tm);
+                        const double d = time_ms(dis, 2, s, tm);
+                        if (a + d < best_ms) {
+                            best_ms = a + d;
+                            bn1 = n1;
+                            bpairs = pairs;
+                            P.tuned_ms[0] = a;
+                            P.tuned_ms[1] = d;
+                        }
+                    }
+                if (P.tc_f34_n1 != bn1 || P.tc_dg1a_pairs != bpairs) {
+                    P.tc_f34_n1 = bn1;
+                    P.tc_dg1a_pairs = bpairs;
+                    tc_replan_shapes(P);
+                }
+            }
         }
         TFMM_CUDA_CHECK(cudaStreamSynchronize(s));
         if (out && tfmm_plan_tuning_get(plan, out) != TFMM_OK) fail(TFMM_INVALID_ARG, last_error());

@@ -75,10 +75,11 @@ class Tuning(ctypes.Structure):
         ("agg_threads", ctypes.c_int32), ("agg_ctas_per_sm", ctypes.c_int32), ("agg_order", ctypes.c_int32),
         ("dis_threads", ctypes.c_int32), ("dis_ctas_per_sm", ctypes.c_int32), ("dis_order", ctypes.c_int32),
         ("agg_blocks", ctypes.c_int32), ("dis_blocks", ctypes.c_int32), ("mrhs_precision", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 3), ("agg_ms", ctypes.c_double), ("dis_ms", ctypes.c_double),
+        ("tc_f34_n1", ctypes.c_int32), ("tc_dg1a_pairs", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1),
+        ("agg_ms", ctypes.c_double), ("dis_ms", ctypes.c_double),
     ]
     _names = ("agg_threads", "agg_ctas_per_sm", "agg_order", "dis_threads", "dis_ctas_per_sm", "dis_order",
-              "agg_blocks", "dis_blocks", "mrhs_precision", "agg_ms", "dis_ms")
+              "agg_blocks", "dis_blocks", "mrhs_precision", "tc_f34_n1", "tc_dg1a_pairs", "agg_ms", "dis_ms")
 
     def as_dict(self):
         return {k: getattr(self, k) for k in self._names}

@@ -282,3 +282,34 @@ def test_items_too_large_for_one_cta_fall_back_to_the_chain():
         for r in range(R):
             assert _rel(spec.cpu().numpy()[r], apply.aggregate_all(T, members, X[r])) <= 1e-5
             assert _rel(y.cpu().numpy()[r], apply.disaggregate_all(T, members, gv[r], n_rwg, w)) <= 1e-5
+
+
+@pytest.mark.parametrize("n1,pairs", [(32, 64), (0, 128), (128, 0), (16, 0)])
+def test_tensor_core_tile_shapes_match_oracle(synth, n1, pairs):
+    """The fused AG3+AG4 block size and the DG1a pair count only change the tiling."""
+    tfmm = _tfmm()
+    plan = synth["plan"]
+    tfmm.tfmm_plan_tuning_set(plan, mrhs_precision=3, tc_f34_n1=n1, tc_dg1a_pairs=pairs)
+    t = tfmm.tfmm_plan_tuning_get(plan)
+    assert (t["tc_f34_n1"], t["tc_dg1a_pairs"], t["mrhs_precision"]) == (n1, pairs, 3)
+    R, G, nd, n = 4, len(synth["members"]), synth["nt"] * synth["npf"], synth["n_rwg"]
+    X = complex_gaussian((R, n), 100 + n1 + pairs)
+    gv = complex_gaussian((R, G, 2, nd), 101 + n1 + pairs)
+    spec = torch.empty((R, G, 2, nd), dtype=torch.complex64, device="cuda")
+    tfmm.tfmm_aggregate(plan, torch.from_numpy(X.astype(np.complex64)).cuda(), spec)
+    y = torch.zeros((R, n), dtype=torch.complex64, device="cuda")
+    tfmm.tfmm_disaggregate(plan, torch.from_numpy(gv.astype(np.complex64)).cuda(), y)
+    tfmm.tfmm_sync(plan)
+    for r in range(R):
+        assert _rel(spec.cpu().numpy()[r], apply.aggregate_all(synth["T"], synth["members"], X[r])) <= 1e-5
+        refy = apply.disaggregate_all(synth["T"], synth["members"], gv[r], n, synth["w"])
+        assert _rel(y.cpu().numpy()[r], refy) <= 1e-5
+    tfmm.tfmm_plan_tuning_set(plan, mrhs_precision=0, tc_f34_n1=0, tc_dg1a_pairs=0)
+
+
+def test_tensor_core_tile_shapes_are_validated(synth):
+    tfmm = _tfmm()
+    for bad in ({"tc_f34_n1": 20}, {"tc_f34_n1": 272}, {"tc_dg1a_pairs": 100}):
+        with pytest.raises(tfmm.TfmmError) as e:
+            tfmm.tfmm_plan_tuning_set(synth["plan"], **bad)
+        assert e.value.status == tfmm.INVALID_ARG
