@@ -193,7 +193,10 @@ tfmm_status tfmm_plan_destroy(tfmm_plan* plan);
  *   x       device, n_rwg x R column-major FP32 complex, leading dimension ldx >= n_rwg
  *   R       1 <= R <= max_rhs
  *   spectra device, R x G x 2 x N_dir FP32 complex, overwritten
- * Errors: INVALID_ARG (null pointers, R out of range, ldx < n_rwg), CUDA. */
+ * R > 1 runs the engine that tfmm_params.mrhs_precision selects; the first call
+ * with a given R and engine allocates its scratch and tile lists (device memory
+ * owned by the plan), later calls allocate nothing.
+ * Errors: INVALID_ARG (null pointers, R out of range, ldx < n_rwg), OOM, CUDA. */
 tfmm_status tfmm_aggregate(tfmm_plan* plan, const tfmm_cfloat* x, int32_t R, int64_t ldx, tfmm_cfloat* spectra,
                            void* stream);
 
