@@ -32,6 +32,10 @@
 //   DG1b H'  (r_t R x r_p)        = P''      . U_phi        A: P'' [a+r_t r][i_phi]  B: U_phi^T [b][i_phi]
 //   DG2  S   (r_b x R)            = C_(3)    . H            A: C_(3) [c][ab]  B: H [r][ab]
 //   DG3  y_g (n_b x R)            = conj(U_beta^(0) S^(0) + U_beta^(1) S^(1))  A: U_beta [n][c]  B: S [r][c]
+// The generic stage kernel (tc_gemm_kernel) runs these as listed.  Two kernels replace
+// steps when the shapes allow: tc_ag34_kernel fuses AG3 and AG4 (V'' never leaves the
+// SM), and tc_dg1a_kernel runs DG1a transposed, U_theta^T as A and 128 (i_phi, r)
+// pairs of the spectra as N, so that its MMAs are wide.
 #include <cuda_bf16.h>
 
 #include <algorithm>
