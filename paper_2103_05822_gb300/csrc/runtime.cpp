@@ -131,6 +131,18 @@ std::unique_ptr<tfmm_plan> load_plan(const char* path, cudaStream_t s) {
     bad(P.params.max_rhs < 1, "params");
     P.n_dir = P.n_theta * P.n_phi;
     P.ld_dir = (int)round_up(P.n_dir, 2);
+    {
+        // the arrays the header announces must fit in what is left of the file (no
+        // allocation sized by a corrupt header)
+        const long here = std::ftell(F.f);
+        std::fseek(F.f, 0, SEEK_END);
+        const long end = std::ftell(F.f);
+        std::fseek(F.f, here, SEEK_SET);
+        const double need = 6.0 * 8 + (2.0 * P.n_theta + P.n_phi) * 8 + 4.0 * P.n_dir + 8.0 * (P.G + 1) +
+                            8.0 * P.N + 24.0 * P.G + 24.0 * P.G + ((head[1] & 1u) ? (double)sizeof(RwgGeom) * P.N : 0.0) +
+                            8;
+        bad(here < 0 || end < 0 || (double)(end - here) < need, "file shorter than its header announces");
+    }
     double sc[6];
     F.get(sc, sizeof(sc));
     P.k = sc[0]; P.w_phi = sc[1];

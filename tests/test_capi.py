@@ -159,3 +159,48 @@ def test_binding_structs_match_the_header(tmp_path):
     want = [ctypes.sizeof(tfmm.Params), ctypes.sizeof(tfmm.PlanInfo), ctypes.sizeof(tfmm.Tuning),
             tfmm.Params.mrhs_precision.offset, tfmm.PlanInfo.kernel_errors.offset, tfmm.Tuning.agg_ms.offset]
     assert got == want
+
+
+def test_checkpoint_header_announcing_huge_arrays_is_refused(lib, tmp_path):
+    """A corrupt header cannot make the loader allocate: sizes are checked against the file."""
+    import struct
+    p = tfmm.tfmm_params_default()
+    head = b"TFMMPLAN" + struct.pack("<III", 1, 0, ctypes.sizeof(tfmm.Params)) + bytes(p)
+    dims = struct.pack("<7i", 10, 11, 22, 1 << 20, 1, 1, 1) + struct.pack("<q", (1 << 31) - 1)
+    f = tmp_path / "huge.tfmm"
+    f.write_bytes(head + dims + bytes(64))
+    with pytest.raises(tfmm.TfmmError) as e:
+        tfmm.tfmm_plan_load(str(f), stream=0)
+    assert e.value.status == tfmm.IO and "shorter" in str(e.value)
+
+
+def test_well_formed_checkpoint_passes_the_header_checks(lib, tmp_path):
+    """A complete file of the documented layout gets past every file check; on a machine
+    without a GPU the load then stops at the first device call (status CUDA, not IO)."""
+    import struct
+    import numpy as np
+    nt, npf, G, N = 2, 3, 1, 2
+    p = tfmm.tfmm_params_default()
+    blob = b"TFMMPLAN" + struct.pack("<III", 1, 2, ctypes.sizeof(tfmm.Params)) + bytes(p)
+    blob += struct.pack("<7i", nt - 1, nt, npf, G, 1, 1, 1) + struct.pack("<q", N)
+    blob += struct.pack("<6d", 2 * np.pi, 2 * np.pi / npf, 0, 0, 0, 0)
+    blob += np.linspace(0.5, 2.5, nt).tobytes() + np.full(nt, 1.0).tobytes() + np.arange(npf, dtype=np.float64).tobytes()
+    blob += np.full(nt * npf, 0.5, np.float32).tobytes()
+    blob += np.array([0, N], np.int64).tobytes() + np.array([1, 0], np.int64).tobytes()
+    blob += np.zeros(3 * G).tobytes() + np.ones(6 * G, np.int32).tobytes()
+    per_alpha = nt + npf + N + 1
+    blob += np.ones(2 * per_alpha, np.complex128).tobytes() + b"TFMMEND."
+    f = tmp_path / "tiny.tfmm"
+    f.write_bytes(blob)
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except ImportError:
+        has_gpu = False
+    if has_gpu:
+        plan = tfmm.tfmm_plan_load(str(f), stream=0)
+        assert plan.info["n_rwg"] == N
+    else:
+        with pytest.raises(tfmm.TfmmError) as e:
+            tfmm.tfmm_plan_load(str(f), stream=0)
+        assert e.value.status == tfmm.CUDA, str(e.value)
