@@ -26,3 +26,18 @@ def test_traffic_record_is_current_and_scales_with_factor_bytes():
 
 def test_whole_job_value_for_one_gpu():
     assert bench.whole_job_ms(200.0, 100, 1) == (200.0, 2.0)
+
+
+def test_default_run_keeps_the_timing_contract(monkeypatch):
+    """No flags: one GPU, the 30-lambda sphere, at least three warm-up steps."""
+    monkeypatch.setattr("sys.argv", ["bench.py"])
+    a = bench.parse()
+    assert a.gpus == 1 and a.workload == "sphere30" and a.impl == "ours"
+    assert a.warmup >= 3 and a.steps >= 50
+
+
+def test_workload_text_names_the_sizes():
+    from paper_2103_05822_gb300.inputs import WORKLOADS
+    txt = bench.workload_desc(WORKLOADS["sphere30"], 39, 40, 80, 1034)
+    for part in ("30 lambda", "972000 RWGs", "40x80", "1034 groups", "1e-06"):
+        assert part in txt, (part, txt)
