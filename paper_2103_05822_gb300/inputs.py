@@ -9,6 +9,13 @@ arithmetic (no basis functions, far-fields, grids or compression) lives here.
   being closed) ``30 nu^2`` interior edges, i.e. RWG basis functions.
   nu = 6 D / lambda gives edges of about lambda / 10, the mesh density of the
   30-lambda sphere of Sec. III.B (940,308 RWGs there, 972,000 here).
+* ``trihedral(edge, n)`` - square trihedral corner reflector: three mutually
+  perpendicular square plates of side ``edge`` meeting at the origin (in the
+  planes x = 0, y = 0, z = 0, each in the positive quadrant), every plate an
+  n x n grid of squares cut into two right triangles.  ``6 n^2`` triangles and
+  ``9 n^2 - 3 n`` interior edges (the three fold edges included), i.e. RWGs;
+  n = 69 at edge = 6 lambda gives 42,642 RWGs, the density of the 42,477-RWG
+  reflector of Sec. III.A.
 * ``complex_gaussian(n, seed)`` - CN(0, 1) vectors: re, im ~ N(0, 1/2).
 * ``synthetic_tucker(...)`` - random cores and factors with prescribed, ragged
   shapes, used to exercise the contraction kernels on their own.
@@ -25,6 +32,8 @@ import numpy as np
 
 __all__ = [
     "icosphere",
+    "trihedral",
+    "workload_mesh",
     "complex_gaussian",
     "synthetic_tucker",
     "Workload",
@@ -128,6 +137,42 @@ def icosphere(diameter: float, nu: int, center=(0.0, 0.0, 0.0)):
     return pos, tris
 
 
+def trihedral(edge: float, n: int):
+    """Square trihedral corner reflector (three plates of side ``edge``, n x n squares each).
+
+    Returns ``(verts, tris)`` like ``icosphere``.  Vertices are the lattice points
+    (i, j, k) h, h = edge / n, with at least one index zero; a point with two zero
+    indices lies on a fold line and belongs to two plates, so the plates are
+    joined along the three axes.
+    """
+    if n < 1:
+        raise ValueError("n must be >= 1")
+    h = edge / n
+    ids = {}
+    pos = []
+
+    def vid(i, j, k):
+        key = (i, j, k)
+        v = ids.get(key)
+        if v is None:
+            v = len(pos)
+            ids[key] = v
+            pos.append((i * h, j * h, k * h))
+        return v
+
+    tris = []
+    # plate z = 0 (x, y), plate y = 0 (x, z), plate x = 0 (y, z)
+    planes = (lambda a, b: (a, b, 0), lambda a, b: (a, 0, b), lambda a, b: (0, a, b))
+    for P in planes:
+        for a in range(n):
+            for b in range(n):
+                p00, p10 = vid(*P(a, b)), vid(*P(a + 1, b))
+                p01, p11 = vid(*P(a, b + 1)), vid(*P(a + 1, b + 1))
+                tris.append((p00, p10, p11))
+                tris.append((p00, p11, p01))
+    return np.asarray(pos, dtype=np.float64), np.asarray(tris, dtype=np.int32)
+
+
 def _edge_point(edges, a, b, step, nu, base_edge):
     """Global id of the point ``step`` lattice steps from ``a`` towards ``b``."""
     key = (min(a, b), max(a, b))
@@ -183,25 +228,38 @@ def synthetic_tucker(n_theta, n_phi, n_beta_list, ranks_list, seed):
 
 @dataclasses.dataclass(frozen=True)
 class Workload:
-    """A PEC-sphere workload: mesh, box grid, FMM accuracy, Tucker tolerance, RHS."""
+    """A PEC workload: mesh, box grid, FMM accuracy, Tucker tolerance, RHS."""
 
     name: str
-    diameter: float      # in wavelengths (lambda = 1, k = 2 pi)
-    nu: int              # icosphere frequency: 20 nu^2 triangles, 30 nu^2 RWGs
+    diameter: float      # sphere diameter, or trihedral plate edge, in wavelengths (lambda = 1, k = 2 pi)
+    nu: int              # icosphere frequency (20 nu^2 triangles, 30 nu^2 RWGs) or squares per plate edge
     box: float           # leaf box edge a, in wavelengths
     digits: int          # FMM accuracy d0
     tol: float           # Tucker tolerance gamma
     nrhs: int            # right-hand sides
-    rhs: str             # "gaussian" | "planewave+gaussian" | "planewave_sweep"
+    rhs: str             # "gaussian" | "planewave+gaussian" | "planewave_sweep" | "planewave_corner"
     seed: int
+    shape: str = "sphere"  # "sphere" | "trihedral"
+    nphi_rule: int = 1     # 1: N_phi = 2(L+1) (the sphere workloads), 0: 2L+1 (the paper's grid)
 
     @property
     def n_tri(self):
+        if self.shape == "trihedral":
+            return 6 * self.nu * self.nu
         return 20 * self.nu * self.nu
 
     @property
     def n_rwg(self):
+        if self.shape == "trihedral":
+            return 9 * self.nu * self.nu - 3 * self.nu
         return 30 * self.nu * self.nu
+
+
+def workload_mesh(w: Workload):
+    """``(verts, tris)`` of a workload's geometry."""
+    if w.shape == "trihedral":
+        return trihedral(w.diameter, w.nu)
+    return icosphere(w.diameter, w.nu)
 
 
 WORKLOADS = {
@@ -212,4 +270,8 @@ WORKLOADS = {
     "sphere20_sweep": Workload("sphere20_sweep", 20.0, 120, 2.0, 6, 1e-6, 16, "gaussian", 5),
     # the 10-lambda sphere with 128 CN(0,1) RHS: a small case of the many-RHS path (profiling)
     "sphere10_rhs128": Workload("sphere10_rhs128", 10.0, 60, 1.0, 6, 1e-6, 128, "gaussian", 6),
+    # the trihedral corner reflector of Sec. III.A: 6-lambda plates, 2-lambda boxes, 5 digits
+    # (L = 37), N_phi = 2L + 1 as in Tables I-II, gamma = 1e-6, the paper's plane wave
+    # (theta_inc = 135 deg, phi_inc = 225 deg, theta-polarised)
+    "corner6": Workload("corner6", 6.0, 69, 2.0, 5, 1e-6, 1, "planewave_corner", 7, shape="trihedral", nphi_rule=0),
 }
