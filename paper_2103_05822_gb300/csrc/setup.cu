@@ -7,14 +7,21 @@
 //
 // HOSVD: the factor of each mode is the leading eigenvector block of the Gram
 // matrix of that mode's unfolding (left singular vectors of the unfolding),
-// truncated where the discarded eigenvalue sum drops to (gamma^2/3) ||A||_F^2,
-// which is the per-mode gamma/sqrt(3) rule of Sec. III.A and gives
-// ||A - A_hat||_F <= gamma ||A||_F.  The modes are processed in the order
+// truncated where the discarded energy drops to (gamma^2/3) ||A||_F^2, which is
+// the per-mode gamma/sqrt(3) rule of Sec. III.A and gives ||A - A_hat||_F <=
+// gamma ||A||_F.  The discarded energy is not read off the Gram's eigenvalues,
+// whose absolute error is of order eps ||A||^2 (the Gram squares the condition
+// number): the energy along each eigenvector v is recomputed from the unfolding
+// itself, ||v^H A_(p)||^2, accurate to order eps ||A|| ||v^H A_(p)||, so tails
+// far below eps ||A||^2 (gamma = 1e-8) are resolved.  The modes are processed in the order
 // theta, phi, beta and each later unfolding is that of the tensor already
 // projected on the earlier factors (sequential truncation; same bound as the
 // plain HOSVD of ref. [26]).  For the beta mode the smaller of the two Gram
 // matrices Z Z^H (n_beta) and Z^H Z (r_theta r_phi) is decomposed; in the
-// second case the factor is re-orthonormalised by a Householder QR.
+// second case the factor is re-orthonormalised by a Householder QR.  For the
+// beta mode a range-limited eigen-solver returns only the eigenvectors above the
+// truncation level while that level is well above the Gram's rounding; below
+// it every eigenvector is computed and the energies come from Z as above.
 #include <cublas_v2.h>
 #include <cusolverDn.h>
 
@@ -25,6 +32,7 @@
 #include <cstring>
 #include <cstdio>
 #include <exception>
+#include <limits>
 #include <memory>
 #include <mutex>
 #include <thread>
@@ -348,6 +356,39 @@ __global__ void sum_parts_kernel(const double2* __restrict__ part, int nparts, i
     }
 }
 
+// count n x n column-reversed identity matrices, back to back: the theta / phi
+// "eigenvectors" of an SVD plan, stored like an eigen-solver's output (ascending),
+// so that take_top_kernel, which reads the columns from the last one back, yields
+// the identity itself.
+__global__ void identity_kernel(double2* __restrict__ G, int n, int count) {
+    const int64_t total = (int64_t)count * n * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e % ((int64_t)n * n);
+        G[e] = make_double2((r % n) == n - 1 - (r / n) ? 1.0 : 0.0, 0.0);
+    }
+}
+
+// out[j] = sum_{i < rows} |E[i + ld j]|^2: one block of 256 threads per column, summed in
+// a fixed order (the ranks chosen from these energies do not depend on timing).
+constexpr int kEnergyThreads = 256;
+__global__ void __launch_bounds__(kEnergyThreads) col_energy_kernel(const double2* __restrict__ E, int64_t rows,
+                                                                    int64_t ld, double* __restrict__ out) {
+    __shared__ double red[kEnergyThreads];
+    const int64_t j = blockIdx.x;
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < rows; i += kEnergyThreads) {
+        const double2 v = E[i + ld * j];
+        acc += v.x * v.x + v.y * v.y;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = kEnergyThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[j] = red[0];
+}
+
 struct Worker {  // one host thread's stream and library handles for per-tensor setup work
     cudaStream_t s = nullptr;
     cublasHandle_t blas = nullptr;
@@ -461,7 +502,12 @@ void hosvd_batch(Plan& P, std::vector<Tensor>& T, std::vector<std::unique_ptr<Wo
     const int nt = P.n_theta, np = P.n_phi;
     const int nT = (int)T.size();
     const int nw = (int)pool.size();
+    // Tucker: gamma / sqrt(3) per mode (Sec. III.A).  SVD (Sec. II.C comparator): the theta
+    // and phi modes are kept whole (identity factors) and the beta mode, whose unfolding is
+    // the transposed aggregation matrix, is truncated at gamma itself (note under Table II).
+    const bool svd = plan_is_svd(P);
     const double tol2 = P.params.tol * P.params.tol / 3.0;
+    const double tol2_beta = svd ? P.params.tol * P.params.tol : tol2;
     const double r_one = 1.0, r_zero = 0.0;
     const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0), zero = make_cuDoubleComplex(0.0, 0.0);
     const char* env = std::getenv("TFMM_EIG");
@@ -475,26 +521,53 @@ void hosvd_batch(Plan& P, std::vector<Tensor>& T, std::vector<std::unique_ptr<Wo
     const int ngmax = std::max(nt, np);
     std::vector<DevBuf> wpart(nw);
     for (auto& b : wpart) b.alloc(sizeof(double2) * (int64_t)(kGramParts + 1) * ngmax * ngmax);
-    parallel_for(pool, nT, [&](Worker& w, int wi, int t) {
-        gram_splitk(w, true, nt, (int64_t)np * T[t].nb, T[t].A, nt, d_G1.as<double2>() + (int64_t)t * nt * nt,
-                    wpart[wi].as<double2>());
-        if (!batched_small)
-            eig_one(w, d_G1.as<double2>() + (int64_t)t * nt * nt, d_W1.as<double>() + (int64_t)t * nt, nt,
-                    winfo[wi].as<int>());
-    });
-    if (batched_small) {
+    if (svd) {
         Worker& w0 = *pool[0];
-        eig_batched(w0.sol, w0.prm, d_G1.as<double2>(), d_W1.as<double>(), nt, nT, w0.s);
+        identity_kernel<<<grid1d((int64_t)nT * nt * nt), 256, 0, w0.s>>>(d_G1.as<double2>(), nt, nT);
+        TFMM_CUDA_CHECK(cudaGetLastError());
+        TFMM_CUDA_CHECK(cudaStreamSynchronize(w0.s));
+    } else {
+        parallel_for(pool, nT, [&](Worker& w, int wi, int t) {
+            gram_splitk(w, true, nt, (int64_t)np * T[t].nb, T[t].A, nt, d_G1.as<double2>() + (int64_t)t * nt * nt,
+                        wpart[wi].as<double2>());
+            if (!batched_small)
+                eig_one(w, d_G1.as<double2>() + (int64_t)t * nt * nt, d_W1.as<double>() + (int64_t)t * nt, nt,
+                        winfo[wi].as<int>());
+        });
+        if (batched_small) {
+            Worker& w0 = *pool[0];
+            eig_batched(w0.sol, w0.prm, d_G1.as<double2>(), d_W1.as<double>(), nt, nT, w0.s);
+        }
     }
-    std::vector<double> W1((size_t)nT * nt);
-    TFMM_CUDA_CHECK(cudaMemcpy(W1.data(), d_W1.p, sizeof(double) * W1.size(), cudaMemcpyDeviceToHost));
+    // Energy of the unfolding along every eigenvector, e_i = ||v_i^H A_(1)||^2, from the
+    // unfolding itself: the Gram's eigenvalues carry absolute errors of order eps ||A||^2,
+    // while these are accurate to order eps ||A|| ||v_i^H A_(1)||, which resolves tails far
+    // below eps ||A||^2 (tolerances near 1e-8).  The ranks are chosen from them.
+    int maxnb = 1;
+    for (int t = 0; t < nT; ++t) maxnb = std::max(maxnb, T[t].nb);
+    std::vector<DevBuf> wA(nw);
+    for (auto& b : wA) b.alloc(sizeof(double2) * (int64_t)nt * np * maxnb);
+    DevBuf d_E1(sizeof(double) * nT * nt);
+    parallel_for(pool, nT, [&](Worker& w, int wi, int t) {
+        // A_(1)^H V (n_phi n_beta x n_theta): elementwise the modulus of V^H A_(1)
+        const int64_t cols = (int64_t)np * T[t].nb;
+        CUBLAS_CHECK(cublasZgemm(w.blas, CUBLAS_OP_C, CUBLAS_OP_N, (int)cols, nt, nt, &one,
+                                 (const cuDoubleComplex*)T[t].A, nt,
+                                 (const cuDoubleComplex*)(d_G1.as<double2>() + (int64_t)t * nt * nt), nt, &zero,
+                                 (cuDoubleComplex*)wA[wi].p, (int)cols));
+        col_energy_kernel<<<nt, kEnergyThreads, 0, w.s>>>(wA[wi].as<double2>(), cols, cols,
+                                                          d_E1.as<double>() + (int64_t)t * nt);
+        TFMM_CUDA_CHECK(cudaGetLastError());
+    });
+    std::vector<double> E1((size_t)nT * nt);
+    TFMM_CUDA_CHECK(cudaMemcpy(E1.data(), d_E1.p, sizeof(double) * E1.size(), cudaMemcpyDeviceToHost));
     int64_t y1_tot = 0;
     std::vector<int64_t> y1_off(nT);
     for (int t = 0; t < nT; ++t) {
         double n2 = 0;
-        for (int i = 0; i < nt; ++i) n2 += std::max(W1[(size_t)t * nt + i], 0.0);
+        for (int i = 0; i < nt; ++i) n2 += E1[(size_t)t * nt + i];
         T[t].norm2 = n2;
-        T[t].rt = choose_rank(&W1[(size_t)t * nt], nt, tol2 * n2);
+        T[t].rt = svd ? nt : choose_rank(&E1[(size_t)t * nt], nt, tol2 * n2);
         y1_off[t] = y1_tot;
         y1_tot += (int64_t)T[t].rt * np * T[t].nb;
     }
@@ -502,12 +575,8 @@ void hosvd_batch(Plan& P, std::vector<Tensor>& T, std::vector<std::unique_ptr<Wo
     t0 = std::chrono::steady_clock::now();
 
     // U_theta; A1 = U_theta^H A_(1) -> [a, i_phi, n]; Y1 = [a, n, i_phi]; G2' = Y1^H Y1
-    int maxnb = 1;
-    for (int t = 0; t < nT; ++t) maxnb = std::max(maxnb, T[t].nb);
     DevBuf d_Ut(sizeof(double2) * nT * nt * nt), d_Y1(sizeof(double2) * std::max<int64_t>(y1_tot, 1));
     DevBuf d_G2(sizeof(double2) * nT * np * np), d_W2(sizeof(double) * nT * np);
-    std::vector<DevBuf> wA(nw);
-    for (auto& b : wA) b.alloc(sizeof(double2) * (int64_t)nt * np * maxnb);
     parallel_for(pool, nT, [&](Worker& w, int wi, int t) {
         const int rt = T[t].rt, nb = T[t].nb;
         double2* Ut = d_Ut.as<double2>() + (int64_t)t * nt * nt;
@@ -518,23 +587,40 @@ void hosvd_batch(Plan& P, std::vector<Tensor>& T, std::vector<std::unique_ptr<Wo
         permute3_kernel<<<grid1d((int64_t)rt * np * nb), 256, 0, w.s>>>(wA[wi].as<double2>(),
                                                                          d_Y1.as<double2>() + y1_off[t], rt, np, nb, 0);
         TFMM_CUDA_CHECK(cudaGetLastError());
+        if (svd) {
+            identity_kernel<<<grid1d((int64_t)np * np), 256, 0, w.s>>>(d_G2.as<double2>() + (int64_t)t * np * np, np, 1);
+            TFMM_CUDA_CHECK(cudaGetLastError());
+            return;
+        }
         gram_splitk(w, false, np, (int64_t)rt * nb, d_Y1.as<double2>() + y1_off[t], (int64_t)rt * nb,
                     d_G2.as<double2>() + (int64_t)t * np * np, wpart[wi].as<double2>());
         if (!batched_small)
             eig_one(w, d_G2.as<double2>() + (int64_t)t * np * np, d_W2.as<double>() + (int64_t)t * np, np,
                     winfo[wi].as<int>());
     });
-    if (batched_small) {
+    if (batched_small && !svd) {
         Worker& w0 = *pool[0];
         eig_batched(w0.sol, w0.prm, d_G2.as<double2>(), d_W2.as<double>(), np, nT, w0.s);
     }
-    std::vector<double> W2((size_t)nT * np);
-    TFMM_CUDA_CHECK(cudaMemcpy(W2.data(), d_W2.p, sizeof(double) * W2.size(), cudaMemcpyDeviceToHost));
+    // energies e_j = ||Y1 v_j||^2 of the theta-projected unfolding along every eigenvector
+    DevBuf d_E2(sizeof(double) * nT * np);
+    parallel_for(pool, nT, [&](Worker& w, int wi, int t) {
+        const int64_t rows = (int64_t)T[t].rt * T[t].nb;
+        CUBLAS_CHECK(cublasZgemm(w.blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)rows, np, np, &one,
+                                 (const cuDoubleComplex*)(d_Y1.as<double2>() + y1_off[t]), (int)rows,
+                                 (const cuDoubleComplex*)(d_G2.as<double2>() + (int64_t)t * np * np), np, &zero,
+                                 (cuDoubleComplex*)wA[wi].p, (int)rows));
+        col_energy_kernel<<<np, kEnergyThreads, 0, w.s>>>(wA[wi].as<double2>(), rows, rows,
+                                                          d_E2.as<double>() + (int64_t)t * np);
+        TFMM_CUDA_CHECK(cudaGetLastError());
+    });
+    std::vector<double> E2((size_t)nT * np);
+    TFMM_CUDA_CHECK(cudaMemcpy(E2.data(), d_E2.p, sizeof(double) * E2.size(), cudaMemcpyDeviceToHost));
     int n3max = 1, mmax = 1;
     for (int t = 0; t < nT; ++t) {
-        T[t].rp = choose_rank(&W2[(size_t)t * np], np, tol2 * T[t].norm2);
+        T[t].rp = svd ? np : choose_rank(&E2[(size_t)t * np], np, tol2 * T[t].norm2);
         double z2 = 0.0;
-        for (int i = np - T[t].rp; i < np; ++i) z2 += std::max(W2[(size_t)t * np + i], 0.0);
+        for (int i = np - T[t].rp; i < np; ++i) z2 += E2[(size_t)t * np + i];
         T[t].z2 = z2;
         mmax = std::max(mmax, T[t].rt * T[t].rp);
         n3max = std::max(n3max, std::min(T[t].nb, T[t].rt * T[t].rp));
@@ -594,6 +680,8 @@ void hosvd_batch(Plan& P, std::vector<Tensor>& T, std::vector<std::unique_ptr<Wo
         weigh[i].resize(eig_h);
     }
     std::vector<double> ms_g(nw, 0.0), ms_e(nw, 0.0), ms_f(nw, 0.0);
+    std::vector<DevBuf> we3(nw);
+    for (auto& b : we3) b.alloc(sizeof(double) * n3max);
     std::vector<std::vector<double>> W3(nT);
     std::vector<int> nvec(nT, 0);  // eigenvectors returned per tensor (ascending, first columns)
     parallel_for(pool, nT, [&](Worker& w, int wi, int t) {
@@ -619,9 +707,14 @@ void hosvd_batch(Plan& P, std::vector<Tensor>& T, std::vector<std::unique_ptr<Wo
         auto tb = std::chrono::steady_clock::now();
         ms_g[wi] += std::chrono::duration<double, std::milli>(tb - ta).count();
         double* Wt = d_W3.as<double>() + (int64_t)t * n3max;
-        const double thr2 = tol2 * T[t].norm2;
+        const double thr2 = tol2_beta * T[t].norm2;
+        // The Gram's eigenvalues resolve discarded energies only down to about eps ||Z||^2 (and
+        // the energy a range-limited solve leaves out is a difference of two such numbers).
+        // When the budget comes within 1000 rounding units of ||Z||^2, decompose fully and take
+        // the energy along each eigenvector from Z itself, as in the theta and phi modes.
+        const bool accurate = thr2 > 0.0 && thr2 < 1e3 * std::numeric_limits<double>::epsilon() * T[t].z2;
         int meig = n;
-        if (use_dx && thr2 > 0.0) {
+        if (use_dx && thr2 > 0.0 && !accurate) {
             double vl = 0.5 * thr2 / n, vu = 2.0 * T[t].z2 + 1.0;
             int64_t meig64 = 0;
             CUSOLVER_CHECK(cusolverDnXsyevdx(w.sol, w.prm, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_V,
@@ -642,11 +735,29 @@ void hosvd_batch(Plan& P, std::vector<Tensor>& T, std::vector<std::unique_ptr<Wo
         TFMM_CUDA_CHECK(cudaStreamSynchronize(w.s));
         if (hinfo != 0) fail(TFMM_NUMERIC, "eigen-decomposition failed (info " + std::to_string(hinfo) + ")");
         if (meig < 1) fail(TFMM_NUMERIC, "no eigenvalue above the truncation bound (zero far-field tensor?)");
-        // energy left out of the returned eigenvalues (all of it below the bound vl)
-        double ret = 0.0;
-        for (double v : W3[t]) ret += std::max(v, 0.0);
-        const double unret = meig < n ? std::max(T[t].z2 - ret, 0.0) : 0.0;
-        T[t].rb = choose_rank(W3[t].data(), meig, thr2, unret);
+        if (accurate) {
+            // e_i: column norms of Z^H V (left eigenvectors, n_beta <= m) or of Z V (right ones)
+            double2* E = wA[wi].as<double2>();
+            if (nb <= m) {
+                CUBLAS_CHECK(cublasZgemm(w.blas, CUBLAS_OP_C, CUBLAS_OP_N, m, nb, nb, &one, (const cuDoubleComplex*)Z,
+                                         nb, (const cuDoubleComplex*)G3, nb, &zero, (cuDoubleComplex*)E, m));
+                col_energy_kernel<<<nb, kEnergyThreads, 0, w.s>>>(E, m, m, we3[wi].as<double>());
+            } else {
+                CUBLAS_CHECK(cublasZgemm(w.blas, CUBLAS_OP_N, CUBLAS_OP_N, nb, m, m, &one, (const cuDoubleComplex*)Z,
+                                         nb, (const cuDoubleComplex*)G3, m, &zero, (cuDoubleComplex*)E, nb));
+                col_energy_kernel<<<m, kEnergyThreads, 0, w.s>>>(E, nb, nb, we3[wi].as<double>());
+            }
+            TFMM_CUDA_CHECK(cudaGetLastError());
+            TFMM_CUDA_CHECK(cudaMemcpyAsync(W3[t].data(), we3[wi].p, sizeof(double) * n, cudaMemcpyDeviceToHost, w.s));
+            TFMM_CUDA_CHECK(cudaStreamSynchronize(w.s));
+            T[t].rb = choose_rank(W3[t].data(), n, thr2);
+        } else {
+            // energy left out of the returned eigenvalues (all of it below the bound vl)
+            double ret = 0.0;
+            for (double v : W3[t]) ret += std::max(v, 0.0);
+            const double unret = meig < n ? std::max(T[t].z2 - ret, 0.0) : 0.0;
+            T[t].rb = choose_rank(W3[t].data(), meig, thr2, unret);
+        }
         nvec[t] = meig;
         ms_e[wi] += ms_since(tb);
     });
@@ -813,7 +924,8 @@ void build_tucker_setup(Plan& P, const Mesh& M, cudaStream_t s) {
     // batches of groups bounded by a device-memory budget
     size_t free_b = 0, total_b = 0;
     TFMM_CUDA_CHECK(cudaMemGetInfo(&free_b, &total_b));
-    const double per_rwg = 16.0 * nd * 2 * 3.2;  // tensors + projections + Grams, both alpha
+    // tensors + projections + Grams, both alpha (an SVD plan keeps its projections whole)
+    const double per_rwg = 16.0 * nd * 2 * (plan_is_svd(P) ? 4.5 : 3.2);
     const double budget = std::min<double>(0.35 * (double)free_b, 48e9);
     int64_t rwg_budget = (int64_t)std::max(1.0, budget / per_rwg);
     if (prm.batch_groups > 0) rwg_budget = INT64_MAX;
