@@ -75,7 +75,13 @@ typedef struct {
                                1 = the single-RHS kernels, one column after another (FP32);
                                2 or 3 = tensor cores with FP32 operands split into 2 or 3
                                BF16 terms (hi + lo [+ lo2]), FP32 accumulation */
-    int32_t reserved[5];
+    int32_t compression; /* 0 = Tucker (Eq. 6, gamma / sqrt(3) per mode); 1 = truncated SVD of
+                            the N_dir x n_beta aggregation matrix at gamma, the comparator of
+                            Sec. II.C and Tables I-IV, stored as a Tucker format with identity
+                            theta / phi factors (r_theta = n_theta, r_phi = n_phi), core
+                            (U_r Sigma_r)^T and U_beta = conj(V_r); its hot path skips the
+                            theta / phi steps and runs the single-RHS kernels for every R */
+    int32_t reserved[4];
 } tfmm_params;
 
 typedef struct {

@@ -183,7 +183,11 @@ struct AggArgs {
     SmemLayout L;
 };
 
-// Aggregation (Fig. 2b) of one (group, alpha) per work item.
+// Aggregation (Fig. 2b) of one (group, alpha) per work item.  SVD: the plan holds
+// the truncated SVD of the aggregation matrix (Sec. II.C comparator) as a Tucker
+// format with identity theta / phi factors, core C_(3) = (U Sigma)^T and U_beta =
+// conj(V): the spectrum is AG1 followed by AG2 written straight to it.
+template <bool SVD>
 __global__ void __launch_bounds__(512) tucker_aggregate_kernel(const AggArgs a) {
     extern __shared__ float4 smem4[];
     float2* sm = reinterpret_cast<float2*>(smem4);
@@ -210,8 +214,10 @@ __global__ void __launch_bounds__(512) tucker_aggregate_kernel(const AggArgs a) 
         }
         for (int r = 0; r < a.R; ++r) {
             // stage the small factors and the group's currents
-            for (int e = tid; e < a.n_theta * d.rt; e += NT) s_ut[(e % a.n_theta) + a.L.ldt * (e / a.n_theta)] = Ut[e];
-            for (int e = tid; e < a.n_phi * d.rp; e += NT) s_up[(e % a.n_phi) + a.L.ldp * (e / a.n_phi)] = Up[e];
+            if (!SVD) {
+                for (int e = tid; e < a.n_theta * d.rt; e += NT) s_ut[(e % a.n_theta) + a.L.ldt * (e / a.n_theta)] = Ut[e];
+                for (int e = tid; e < a.n_phi * d.rp; e += NT) s_up[(e % a.n_phi) + a.L.ldp * (e / a.n_phi)] = Up[e];
+            }
             for (int n = tid; n < d.ld_nb; n += NT)
                 s_x[n] = n < d.n_beta ? a.x[(int64_t)a.grp_rwg[d.rwg + n] + a.ldx * r] : make_float2(0.f, 0.f);
             __syncthreads();
@@ -219,6 +225,16 @@ __global__ void __launch_bounds__(512) tucker_aggregate_kernel(const AggArgs a) 
             rowdot<false>(reinterpret_cast<const float4*>(Ub), d.ld_nb / 2, d.rb, reinterpret_cast<const float4*>(s_x),
                           [&](int c, float2 v) { s_t[c] = v; });
             __syncthreads();
+            if (SVD) {
+                // F[i] = sum_c B[i, c] t[c], i = i_theta + n_theta i_phi (the core's column index)
+                float2* out = a.spec + (((int64_t)r * a.G + d.g) * 2 + d.alpha) * a.n_dir;
+                rowaxpy(reinterpret_cast<const float4*>(Cc), d.ld_ab / 2, d.rb, s_t, s_part, [&](int j, float4 v) {
+                    out[2 * j] = make_float2(v.x, v.y);
+                    if (2 * j + 1 < a.n_dir) out[2 * j + 1] = make_float2(v.z, v.w);
+                });
+                __syncthreads();
+                continue;
+            }
             // AG2: M[ab] = sum_c C_(3)[c, ab] t[c]
             rowaxpy(reinterpret_cast<const float4*>(Cc), d.ld_ab / 2, d.rb, s_t, s_part,
                     [&](int j, float4 v) { reinterpret_cast<float4*>(s_M)[j] = v; });
@@ -261,7 +277,9 @@ struct DisArgs {
     SmemLayout L;
 };
 
-// Disaggregation (Fig. 3b) of one group (both alpha) per work item.
+// Disaggregation (Fig. 3b) of one group (both alpha) per work item.  SVD (see the
+// aggregation): H is conj(W g) itself, then DG2 and DG3.
+template <bool SVD>
 __global__ void __launch_bounds__(512, 3) tucker_disaggregate_kernel(const DisArgs a) {
     extern __shared__ float4 smem4[];
     float2* sm = reinterpret_cast<float2*>(smem4);
@@ -294,6 +312,18 @@ __global__ void __launch_bounds__(512, 3) tucker_disaggregate_kernel(const DisAr
                     prefetch_head_l2(Cc, (int64_t)d.rb * d.ld_ab * 8);
                     prefetch_head_l2(Ub, (int64_t)d.rb * d.ld_nb * 8);
                 }
+                if (SVD) {
+                    for (int o = tid; o < d.ld_ab; o += NT) {
+                        float2 v = make_float2(0.f, 0.f);
+                        if (o < a.n_dir) {
+                            const float2 gv = gin[o];
+                            const float wt = a.w ? a.w[o] : 1.0f;
+                            v = make_float2(wt * gv.x, -wt * gv.y);
+                        }
+                        s_H[o] = v;
+                    }
+                    __syncthreads();
+                } else {
                 for (int e = tid; e < a.n_theta * d.rt; e += NT) s_ut[(e % a.n_theta) + a.L.ldt * (e / a.n_theta)] = Ut[e];
                 for (int e = tid; e < a.n_phi * d.rp; e += NT) s_up[(e % a.n_phi) + a.L.ldp * (e / a.n_phi)] = Up[e];
                 for (int o = tid; o < a.n_dir; o += NT) {
@@ -319,6 +349,7 @@ __global__ void __launch_bounds__(512, 3) tucker_disaggregate_kernel(const DisAr
                     s_H[o] = acc;
                 }
                 __syncthreads();
+                }
                 // DG2: s[c] = sum_ab C_(3)[c, ab] H[ab]
                 rowdot<false>(reinterpret_cast<const float4*>(Cc), d.ld_ab / 2, d.rb,
                               reinterpret_cast<const float4*>(s_H), [&](int c, float2 v) { s_s[c] = v; });
@@ -490,6 +521,31 @@ SmemLayout agg_layout(const Plan& P, int NT) {
     return L;
 }
 
+// SVD plans: x (or y), t (or s), the core row buffer H (N_dir, disaggregation) and the
+// rowaxpy scratch; no theta / phi factors are staged.
+SmemLayout svd_agg_layout(const Plan& P, int NT) {
+    SmemLayout L{};
+    int o = 0;
+    L.o_a = L.o_b = L.o_e = 0;
+    L.o_c = o; o += al16(P.max_ldnb);
+    L.o_d = o; o += al16(P.max_rank[2]);
+    L.o_f = o; o += 2 * NT;
+    L.total = o;
+    return L;
+}
+
+SmemLayout svd_dis_layout(const Plan& P, int NT) {
+    SmemLayout L{};
+    int o = 0;
+    L.o_a = L.o_b = L.o_g = 0;
+    L.o_c = o; o += al16(P.max_ldnb);
+    L.o_d = o; o += al16(P.max_ldab);
+    L.o_e = o; o += al16(P.max_rank[2]);
+    L.o_f = o; o += 2 * NT;
+    L.total = o;
+    return L;
+}
+
 SmemLayout dis_layout(const Plan& P, int NT) {
     SmemLayout L{};
     L.ldt = odd_ld(P.n_theta);
@@ -563,7 +619,8 @@ void pack_factors_fp32(Plan& P, cudaStream_t s) {
             d.core = take((int64_t)d.rb * d.ld_ab);
             d.uphi = take((int64_t)np * d.rp);
             d.uth = take((int64_t)nt * d.rt);
-            alg += (int64_t)d.rb * d.n_beta + (int64_t)d.rb * d.rt * d.rp + (int64_t)np * d.rp + (int64_t)nt * d.rt;
+            alg += (int64_t)d.rb * d.n_beta + (int64_t)d.rb * d.rt * d.rp;
+            if (!plan_is_svd(P)) alg += (int64_t)np * d.rp + (int64_t)nt * d.rt;
             P.max_nb = std::max(P.max_nb, d.n_beta);
             P.max_ldnb = std::max(P.max_ldnb, d.ld_nb);
             P.max_ldab = std::max(P.max_ldab, d.ld_ab);
@@ -631,10 +688,21 @@ void configure_hot(Plan& P, const HotTuning& t, cudaStream_t s) {
     // stream-ordered: launches already queued keep reading the old order until these copies land
     TFMM_CUDA_CHECK(cudaMemcpyAsync(P.d_agg_order, agg.data(), sizeof(int) * nI, cudaMemcpyHostToDevice, s));
     TFMM_CUDA_CHECK(cudaMemcpyAsync(P.d_dis_order, dis.data(), sizeof(int) * P.G, cudaMemcpyHostToDevice, s));
-    P.agg_sched = make_schedule(tucker_aggregate_kernel, t.agg_threads,
-                                sizeof(float2) * agg_layout(P, t.agg_threads).total, P.num_sms, nI, t.agg_ctas_per_sm);
-    P.dis_sched = make_schedule(tucker_disaggregate_kernel, t.dis_threads,
-                                sizeof(float2) * dis_layout(P, t.dis_threads).total, P.num_sms, P.G, t.dis_ctas_per_sm);
+    if (plan_is_svd(P)) {
+        P.agg_sched = make_schedule(tucker_aggregate_kernel<true>, t.agg_threads,
+                                    sizeof(float2) * svd_agg_layout(P, t.agg_threads).total, P.num_sms, nI,
+                                    t.agg_ctas_per_sm);
+        P.dis_sched = make_schedule(tucker_disaggregate_kernel<true>, t.dis_threads,
+                                    sizeof(float2) * svd_dis_layout(P, t.dis_threads).total, P.num_sms, P.G,
+                                    t.dis_ctas_per_sm);
+    } else {
+        P.agg_sched = make_schedule(tucker_aggregate_kernel<false>, t.agg_threads,
+                                    sizeof(float2) * agg_layout(P, t.agg_threads).total, P.num_sms, nI,
+                                    t.agg_ctas_per_sm);
+        P.dis_sched = make_schedule(tucker_disaggregate_kernel<false>, t.dis_threads,
+                                    sizeof(float2) * dis_layout(P, t.dis_threads).total, P.num_sms, P.G,
+                                    t.dis_ctas_per_sm);
+    }
     P.tuning = t;
     P.hot_ok = P.agg_sched.blocks > 0 && P.dis_sched.blocks > 0;
     TFMM_CUDA_CHECK(cudaStreamSynchronize(s));
@@ -696,8 +764,13 @@ void launch_tucker_aggregate(const Plan& P, const float2* x, int R, int64_t ldx,
     a.R = R;
     a.ctr = P.d_counters + 0;
     a.done = P.d_counters + 1;
-    a.L = agg_layout(P, P.agg_sched.threads);
-    tucker_aggregate_kernel<<<P.agg_sched.blocks, P.agg_sched.threads, P.agg_sched.smem, s>>>(a);
+    if (plan_is_svd(P)) {
+        a.L = svd_agg_layout(P, P.agg_sched.threads);
+        tucker_aggregate_kernel<true><<<P.agg_sched.blocks, P.agg_sched.threads, P.agg_sched.smem, s>>>(a);
+    } else {
+        a.L = agg_layout(P, P.agg_sched.threads);
+        tucker_aggregate_kernel<false><<<P.agg_sched.blocks, P.agg_sched.threads, P.agg_sched.smem, s>>>(a);
+    }
     TFMM_CUDA_CHECK(cudaGetLastError());
 }
 
@@ -722,8 +795,13 @@ void launch_tucker_disaggregate(const Plan& P, const float2* spec, int R, int we
     a.R = R;
     a.ctr = P.d_counters + 2;
     a.done = P.d_counters + 3;
-    a.L = dis_layout(P, P.dis_sched.threads);
-    tucker_disaggregate_kernel<<<P.dis_sched.blocks, P.dis_sched.threads, P.dis_sched.smem, s>>>(a);
+    if (plan_is_svd(P)) {
+        a.L = svd_dis_layout(P, P.dis_sched.threads);
+        tucker_disaggregate_kernel<true><<<P.dis_sched.blocks, P.dis_sched.threads, P.dis_sched.smem, s>>>(a);
+    } else {
+        a.L = dis_layout(P, P.dis_sched.threads);
+        tucker_disaggregate_kernel<false><<<P.dis_sched.blocks, P.dis_sched.threads, P.dis_sched.smem, s>>>(a);
+    }
     TFMM_CUDA_CHECK(cudaGetLastError());
 }
 

@@ -305,6 +305,9 @@ void pack_dense_fp32_from_f64(Plan& P, const double2* src, int g, int alpha, cud
 
 inline int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
+// The plan holds the truncated SVD of the aggregation matrices (identity theta / phi factors).
+inline bool plan_is_svd(const Plan& P) { return P.params.compression == 1; }
+
 }  // namespace tfmm
 
 struct tfmm_mesh {

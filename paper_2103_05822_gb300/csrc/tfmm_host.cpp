@@ -156,6 +156,7 @@ void check_params(const tfmm_params& p) {
     TFMM_REQUIRE(p.max_rhs >= 1, "max_rhs must be >= 1");
     TFMM_REQUIRE(p.batch_groups >= 0, "batch_groups must be >= 0");
     TFMM_REQUIRE(p.mrhs_precision >= 0 && p.mrhs_precision <= 3, "mrhs_precision must be 0, 1, 2 or 3");
+    TFMM_REQUIRE(p.compression == 0 || p.compression == 1, "compression must be 0 (Tucker) or 1 (SVD)");
 }
 
 // The engine that applies one call with R columns:
@@ -171,7 +172,7 @@ Engine engine_for(const Plan& P, int R, int* terms) {
     const int p = P.params.mrhs_precision;
     const char* e = std::getenv("TFMM_MR");
     const bool loop = e && std::strcmp(e, "loop") == 0;
-    if (P.hot_ok && (R <= 1 || loop || p == 1)) return Engine::columns;
+    if (P.hot_ok && (R <= 1 || loop || p == 1 || plan_is_svd(P))) return Engine::columns;
     if (R > 1 && (p == 2 || p == 3)) {
         *terms = p;
         return Engine::tc;

@@ -17,6 +17,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libtfmm.so
 _lib = None
 
 OK, INVALID_ARG, OOM, CUDA, NUMERIC, NOT_BUILT, IO = range(7)
+TUCKER, SVD = 0, 1  # tfmm_params.compression
 
 EXPORTED = [
     "tfmm_params_default", "tfmm_last_error",
@@ -47,7 +48,8 @@ class Params(ctypes.Structure):
         ("k", ctypes.c_double), ("box", ctypes.c_double), ("digits", ctypes.c_double),
         ("nphi_rule", ctypes.c_int32), ("L_override", ctypes.c_int32), ("tol", ctypes.c_double),
         ("quad_order", ctypes.c_int32), ("keep_dense", ctypes.c_int32), ("max_rhs", ctypes.c_int32),
-        ("batch_groups", ctypes.c_int32), ("mrhs_precision", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5),
+        ("batch_groups", ctypes.c_int32), ("mrhs_precision", ctypes.c_int32), ("compression", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 4),
     ]
 
 

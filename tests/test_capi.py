@@ -149,15 +149,16 @@ def test_binding_structs_match_the_header(tmp_path):
         '#include <stdio.h>\n#include <stddef.h>\n#include "tfmm.h"\n'
         'int main(void) {\n'
         '  printf("%zu %zu %zu\\n", sizeof(tfmm_params), sizeof(tfmm_plan_info), sizeof(tfmm_tuning));\n'
-        '  printf("%zu %zu %zu\\n", offsetof(tfmm_params, mrhs_precision), offsetof(tfmm_plan_info, kernel_errors),\n'
-        '         offsetof(tfmm_tuning, agg_ms));\n'
+        '  printf("%zu %zu %zu %zu\\n", offsetof(tfmm_params, mrhs_precision), offsetof(tfmm_params, compression),\n'
+        '         offsetof(tfmm_plan_info, kernel_errors), offsetof(tfmm_tuning, agg_ms));\n'
         '  return 0;\n}\n')
     exe = tmp_path / "sizes"
     subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
     got = [int(v) for v in out]
     want = [ctypes.sizeof(tfmm.Params), ctypes.sizeof(tfmm.PlanInfo), ctypes.sizeof(tfmm.Tuning),
-            tfmm.Params.mrhs_precision.offset, tfmm.PlanInfo.kernel_errors.offset, tfmm.Tuning.agg_ms.offset]
+            tfmm.Params.mrhs_precision.offset, tfmm.Params.compression.offset, tfmm.PlanInfo.kernel_errors.offset,
+            tfmm.Tuning.agg_ms.offset]
     assert got == want
 
 
