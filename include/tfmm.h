@@ -251,9 +251,13 @@ tfmm_status tfmm_planewave(const tfmm_plan* plan, const double* khat, const doub
  * synchronisation a cudaFree implies.  Instead of a per-call allocation, the
  * incidence table is staged in one fixed array inside the library: at most
  * 1024 incidences (48 KiB), present on every GPU that loads the library until
- * the process exits.  The call allocates and frees nothing and returns without
- * synchronising the stream.
- *   khat, pol  host, R x 3, as tfmm_planewave (copied before the call returns)
+ * the process exits.  The call allocates and frees no memory.  khat and pol are
+ * first copied into a fixed host array of the library (ordinary pageable
+ * memory) and from there to the device table, so the caller may reuse or free
+ * its arrays, pinned or not, as soon as the call returns; a copy from pageable
+ * memory may make the call wait for work queued earlier on `stream`.  The
+ * kernel itself is queued on `stream` without waiting for it.
+ *   khat, pol  host, R x 3, as tfmm_planewave
  *   V          device, n_rwg x R FP32 complex, overwritten
  *   R          1..1024; a larger R returns INVALID_ARG with a message
  * The first call on a device looks up the device address of the table (once

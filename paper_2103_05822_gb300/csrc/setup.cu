@@ -1093,6 +1093,14 @@ static __device__ __align__(256) double g_pw_table[6 * kNoAllocMaxIncidences];
 namespace {
 std::mutex g_pw_table_mu;
 double* g_pw_table_addr[256] = {};
+// Host staging copy of the incidence table.  The caller's khat / pol may be
+// pinned, in which case a copy straight from them could still be in flight
+// when the call returns; this array is ordinary pageable memory, which
+// cudaMemcpyAsync has consumed (copied to its own staging area) by the time it
+// returns, so the caller may reuse its arrays at once.  Guarded by
+// g_pw_stage_mu for the duration of the two copies.
+std::mutex g_pw_stage_mu;
+double g_pw_stage[6 * kNoAllocMaxIncidences];
 
 // Device address of g_pw_table on the current device, looked up once per device
 // (a host-side reference to g_pw_table is only a stand-in, not that address).
@@ -1118,9 +1126,14 @@ void planewave_rhs_noalloc(const Plan& P, const double* khat, const double* pol,
     double* table = pw_table_address();
     upload_quadrature(P.params.quad_order, s);
     // every entry the kernel reads is overwritten here: nothing has to start at zero
-    TFMM_CUDA_CHECK(cudaMemcpyAsync(table, khat, sizeof(double) * 3 * R, cudaMemcpyHostToDevice, s));
-    TFMM_CUDA_CHECK(cudaMemcpyAsync(table + 3 * kNoAllocMaxIncidences, pol, sizeof(double) * 3 * R,
-                                    cudaMemcpyHostToDevice, s));
+    {
+        std::lock_guard<std::mutex> lock(g_pw_stage_mu);
+        std::memcpy(g_pw_stage, khat, sizeof(double) * 3 * R);
+        std::memcpy(g_pw_stage + 3 * kNoAllocMaxIncidences, pol, sizeof(double) * 3 * R);
+        TFMM_CUDA_CHECK(cudaMemcpyAsync(table, g_pw_stage, sizeof(double) * 3 * R, cudaMemcpyHostToDevice, s));
+        TFMM_CUDA_CHECK(cudaMemcpyAsync(table + 3 * kNoAllocMaxIncidences, g_pw_stage + 3 * kNoAllocMaxIncidences,
+                                        sizeof(double) * 3 * R, cudaMemcpyHostToDevice, s));
+    }
     PWArgs a;
     a.geom = P.d_geom;
     a.khat = table;

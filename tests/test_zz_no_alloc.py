@@ -50,6 +50,41 @@ def test_noalloc_planewave_matches_allocating_entry_point():
         assert err <= TOL, (R, err)
 
 
+def test_noalloc_planewave_allocates_nothing_and_frees_caller_arrays_at_once():
+    """Pinned caller arrays may be overwritten as soon as the call returns, and a
+    call after the first (which looks up the table's device address) leaves the
+    device's free memory unchanged."""
+    from paper_2103_05822_gb300 import tfmm
+    from paper_2103_05822_gb300.inputs import icosphere
+
+    v, f = icosphere(1.0, 4)
+    mesh = tfmm.tfmm_mesh_create(v, f)
+    plan = tfmm.tfmm_plan_create(mesh, tfmm.tfmm_params_default(box=0.5, digits=3.0, tol=1e-4))
+    n = plan.info["n_rwg"]
+    rng = np.random.default_rng(7)
+    R = 64
+    k, pol = _incidences(rng, R)
+    ref = torch.empty((R, n), dtype=torch.complex64, device="cuda")
+    got = torch.full((R, n), float("nan"), dtype=torch.complex64, device="cuda")
+    tfmm.tfmm_planewave(plan, k, pol, ref)
+    tfmm.tfmm_planewave_noalloc(plan, k, pol, got)  # first call on this device: set-up
+    torch.cuda.synchronize()
+    kp = torch.empty((R, 3), dtype=torch.float64).pin_memory()
+    pp = torch.empty((R, 3), dtype=torch.float64).pin_memory()
+    kp.numpy()[:] = k
+    pp.numpy()[:] = pol
+    got.fill_(float("nan"))
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
+    tfmm.tfmm_planewave_noalloc(plan, kp.numpy(), pp.numpy(), got)
+    kp.fill_(float("nan"))  # the caller reuses its pinned arrays at once
+    pp.fill_(float("nan"))
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free_before
+    err = float(torch.linalg.vector_norm(got - ref) / torch.linalg.vector_norm(ref))
+    assert err <= TOL, err
+
+
 def test_noalloc_planewave_rejects_more_incidences_than_the_table_holds():
     from paper_2103_05822_gb300 import tfmm
     from paper_2103_05822_gb300.inputs import icosphere
