@@ -218,8 +218,9 @@ __device__ __forceinline__ void load_g_tile(uint8_t* st, const TcCtx& c, const T
     }
 }
 
-// Loads k-tile `kt` of the problem's A (128 rows from m0) and B (BN rows from n0) into one stage.
-template <int T, int S>
+// Loads k-tile `kt` of the problem's A (128 rows from m0) and B (BN rows from n0) into one
+// stage, NTHR threads sharing the copies.
+template <int T, int S, int NTHR = TTHREADS>
 __device__ __forceinline__ void load_stage(uint8_t* st, const TcCtx& c, const TcProb& p, int m0, int n0, int kt,
                                            int kt0) {
     const bool seg1 = kt >= kt0;
@@ -231,8 +232,11 @@ __device__ __forceinline__ void load_stage(uint8_t* st, const TcCtx& c, const Tc
     const int64_t ald = seg1 ? p.a_ld1 : p.a_ld0, aps = seg1 ? p.a_ps1 : p.a_ps0;
     const int64_t bld = seg1 ? p.b_ld1 : p.b_ld0, bps = seg1 ? p.b_ps1 : p.b_ps0;
     const int na = (S == TDG1A && c.spec_in) ? 0 : 2 * T * TBM * 4;
-    if (S == TDG1A && c.spec_in) load_g_tile<T>(st, c, p, m0, k0);
-    for (int idx = threadIdx.x; idx < na; idx += TTHREADS) {
+    if constexpr (S == TDG1A) {
+        static_assert(NTHR == TTHREADS, "the spectra tile loader assumes one 128-thread CTA");
+        if (c.spec_in) load_g_tile<T>(st, c, p, m0, k0);
+    }
+    for (int idx = threadIdx.x; idx < na; idx += NTHR) {
         const int pl = idx / (TBM * 4), rem = idx % (TBM * 4), r = rem >> 2, kc = rem & 3;
         const int m = m0 + r, k = k0 + kc * 8;
         const bool ok = m < p.M && k < K8;
@@ -241,7 +245,7 @@ __device__ __forceinline__ void load_stage(uint8_t* st, const TcCtx& c, const Tc
     }
     const int nb = 2 * T * p.BN * 4;
     uint8_t* sb = st + 2 * T * PLANE_TILE;
-    for (int idx = threadIdx.x; idx < nb; idx += TTHREADS) {
+    for (int idx = threadIdx.x; idx < nb; idx += NTHR) {
         const int pl = idx / (p.BN * 4), rem = idx % (p.BN * 4), r = rem >> 2, kc = rem & 3;
         const int n = n0 + r, k = k0 + kc * 8;
         const bool ok = n < p.N && k < K8;
@@ -294,14 +298,44 @@ __device__ __forceinline__ void epilogue(const TcCtx& c, const TcProb& p, int i,
     }
 }
 
+// Adds 64 columns (from col) of the accumulator pair at TMEM column `base` (re) and
+// base + cofs (im) of this warp's lane quarter into registers; columns past bn skipped.
+__device__ __forceinline__ void drain_add(float (&ar)[64], float (&ai)[64], uint32_t base, int cofs, int col,
+                                          int bn) {
+#pragma unroll
+    for (int c0 = 0; c0 < 64; c0 += 32) {
+        if (col + c0 < bn) {  // warp-uniform
+            uint32_t vr[32], vi[32];
+            tmem_ld32(vr, base + col + c0);
+            tmem_ld32(vi, base + cofs + col + c0);
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                ar[c0 + j] += __uint_as_float(vr[j]);
+                ai[c0 + j] += __uint_as_float(vi[j]);
+            }
+        }
+    }
+}
+
 // nst: stages of the shared-memory ring (1 .. NST_MAX); tcols: TMEM columns allocated
 // (Cr at column 0, Ci at column cofs).
-template <int T, int S>
-__global__ void __launch_bounds__(TTHREADS) tc_gemm_kernel(const TcCtx c, const TcProb* __restrict__ probs,
-                                                          const MrTile* __restrict__ tiles, int nst, int tcols,
-                                                          int cofs, int hsplit) {
+//
+// CH (chunked accumulation, needs hsplit): the accumulation in TMEM rounds toward
+// zero at every MMA, so its error grows with the number of K steps summed into one
+// accumulator.  With CH the leading products (hi x hi) start a fresh accumulator
+// every `chunk` k-tiles; at the end of each chunk the CTA waits for its MMAs and
+// adds the accumulator into FP32 registers (round to nearest), so no accumulator
+// sees more than 2 chunk K steps of 16.  The correction products, 2^-8 smaller,
+// stay in one accumulator over the whole K.  Eight warps: warps w and w + 4 read
+// lane quarter w & 3 of TMEM and hold 64 columns each.
+template <int T, int S, bool CH>
+__global__ void __launch_bounds__(CH ? 2 * TTHREADS : TTHREADS)
+    tc_gemm_kernel(const TcCtx c, const TcProb* __restrict__ probs, const MrTile* __restrict__ tiles, int nst,
+                   int tcols, int cofs, int hsplit, int chunk) {
     constexpr int NST_MAX = (T == 2) ? 3 : 2;
     constexpr int STAGE = 2 * 2 * T * PLANE_TILE;
+    constexpr int NTHR = CH ? 2 * TTHREADS : TTHREADS;
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t mbar[NST_MAX];
     __shared__ uint32_t tmem_base;
@@ -325,10 +359,18 @@ __global__ void __launch_bounds__(TTHREADS) tc_gemm_kernel(const TcCtx c, const 
     const int KT = kt0 + (p.K1 > 0 ? (p.K1 + TBK - 1) / TBK : 0);
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(p.BN >> 3) << 17) | ((uint32_t)(TBM >> 4) << 24);
     const uint32_t idesc_neg = idesc | (1u << 13);
+    // CH: this warp's TMEM lanes and 64 columns, and their running FP32 sums
+    const uint32_t q_lanes = (uint32_t)((warp & 3) * 32) << 16;
+    const int q_col = (warp >> 2) * 64;
+    float accr[CH ? 64 : 1], acci[CH ? 64 : 1];
+    if constexpr (CH) {
+#pragma unroll
+        for (int j = 0; j < 64; ++j) accr[j] = acci[j] = 0.f;
+    }
     bool ok = true;
     // prologue: k-tiles 0 .. NST-2
     for (int s = 0; s < NST - 1; ++s) {
-        if (s < KT) load_stage<T, S>(smem + s * STAGE, c, p, t.m0, t.n0, s, kt0);
+        if (s < KT) load_stage<T, S, NTHR>(smem + s * STAGE, c, p, t.m0, t.n0, s, kt0);
         asm volatile("cp.async.commit_group;");
     }
     (void)STAGE;
@@ -336,7 +378,7 @@ __global__ void __launch_bounds__(TTHREADS) tc_gemm_kernel(const TcCtx c, const 
         const int b = kt % NST;
         if (NST == 1) {  // single buffer: reload it once the previous k-tile's MMAs are done
             if (kt >= 1) ok = ok && mbar_wait(&mbar[0], (kt - 1) & 1);
-            if (ok) load_stage<T, S>(smem, c, p, t.m0, t.n0, kt, kt0);
+            if (ok) load_stage<T, S, NTHR>(smem, c, p, t.m0, t.n0, kt, kt0);
             asm volatile("cp.async.commit_group;");
             asm volatile("cp.async.wait_group 0;");
         } else if (NST == 2) {
@@ -353,6 +395,7 @@ __global__ void __launch_bounds__(TTHREADS) tc_gemm_kernel(const TcCtx c, const 
             // K steps of 16 that hold data in this k-tile (the zero tail past K is skipped)
             const int kseg = kt >= kt0 ? p.K1 : p.K0, koff = (kt >= kt0 ? kt - kt0 : kt) * TBK;
             const int nsteps = min(2, (kseg - koff + 15) / 16);
+            const bool fresh = CH && (kt % chunk) == 0;  // first k-tile of a chunk
 #pragma unroll
             for (int s16 = 0; s16 < 2; ++s16)
 #pragma unroll
@@ -365,7 +408,8 @@ __global__ void __launch_bounds__(TTHREADS) tc_gemm_kernel(const TcCtx c, const 
                     // hsplit: the leading product (hi x hi) and the correction products
                     // accumulate apart (columns 0 / 2 cofs), summed in FP32 by the epilogue
                     const bool lo = hsplit && q > 0;
-                    const uint32_t acc = (kt > 0 || s16 > 0 || q > (lo ? 1 : 0) || (q > 0 && !hsplit)) ? 1u : 0u;
+                    uint32_t acc = (kt > 0 || s16 > 0 || q > (lo ? 1 : 0) || (q > 0 && !hsplit)) ? 1u : 0u;
+                    if (CH && !lo) acc = (fresh && s16 == 0) ? 0u : 1u;
                     const uint32_t d = tm + (lo ? 2 * cofs : 0);
                     mma_bf16(d, make_desc(ar), make_desc(br), idesc, acc);
                     mma_bf16(d, make_desc(ai), make_desc(bi), idesc_neg, 1u);
@@ -380,9 +424,20 @@ __global__ void __launch_bounds__(TTHREADS) tc_gemm_kernel(const TcCtx c, const 
             const int nk = kt + NST - 1;
             if (nk < KT) {
                 if (kt >= 1) ok = ok && mbar_wait(&mbar[(kt - 1) % NST], ((kt - 1) / NST) & 1);
-                if (ok) load_stage<T, S>(smem + (nk % NST) * STAGE, c, p, t.m0, t.n0, nk, kt0);
+                if (ok) load_stage<T, S, NTHR>(smem + (nk % NST) * STAGE, c, p, t.m0, t.n0, nk, kt0);
             }
             asm volatile("cp.async.commit_group;");
+        }
+        if constexpr (CH) {
+            if (kt % chunk == chunk - 1 && kt + 1 < KT) {
+                // end of a chunk: once its MMAs are done, add the leading-product
+                // accumulator into the registers; the next k-tile restarts it
+                ok = mbar_wait(&mbar[b], (kt / NST) & 1) && ok;
+                ok = __syncthreads_and(ok);
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                if (ok) drain_add(accr, acci, tm + q_lanes, cofs, q_col, p.BN);
+                asm volatile("tcgen05.fence::before_thread_sync;");
+            }
         }
     }
     asm volatile("cp.async.wait_group 0;");
@@ -393,6 +448,18 @@ __global__ void __launch_bounds__(TTHREADS) tc_gemm_kernel(const TcCtx c, const 
     ok = __syncthreads_and(ok);
     if (!ok) {
         if (tid == 0) atomicAdd(c.err, 1);
+    } else if constexpr (CH) {
+        // the last chunk and the correction products, then the outputs from registers
+        drain_add(accr, acci, tm + q_lanes, cofs, q_col, p.BN);
+        drain_add(accr, acci, tm + q_lanes + 2 * cofs, cofs, q_col, p.BN);
+        const int row = t.m0 + (warp & 3) * 32 + lane;
+        if (row < p.M) {
+#pragma unroll
+            for (int jj = 0; jj < 64; ++jj) {
+                const int cc = q_col + jj, col = t.n0 + cc;
+                if (cc < p.BN && col < p.N) epilogue<T, S>(c, p, row, col, make_float2(accr[jj], acci[jj]));
+            }
+        }
     } else {
         const int row = t.m0 + warp * 32 + lane;
         for (int c0 = 0; c0 < p.BN; c0 += 32) {
@@ -467,6 +534,17 @@ __device__ __forceinline__ void load_planes(uint8_t* dst, int plane_bytes, int K
     }
 }
 
+// The accumulation in TMEM rounds toward zero at every MMA, relative to the
+// accumulator's current magnitude.  With the whole K in shared memory, the kernels
+// below issue every correction product (2^-8 smaller than the leading hi x hi
+// product) over all K steps first, while the accumulator is still small, and the
+// leading products last: the leading accumulation then sees only 2 MMAs per K step
+// at full scale, as with a separate accumulator, without its TMEM columns.
+template <int T>
+__device__ __forceinline__ int product_order(int i) {  // corrections first, hi x hi last
+    return i + 1 < n_products<T>() ? i + 1 : 0;
+}
+
 template <int T>
 __device__ __forceinline__ void issue_products(uint32_t d_re, uint32_t d_im, uint32_t a, int a_plane, uint32_t b,
                                                int b_plane, uint32_t sbo_a, uint32_t sbo_b, int ksteps,
@@ -476,17 +554,19 @@ __device__ __forceinline__ void issue_products(uint32_t d_re, uint32_t d_im, uin
     // the start-address field holds addr >> 4 (shared memory < 256 KB): offsets add to it
     const uint64_t da = make_desc_sbo(a, sbo_a), db = make_desc_sbo(b, sbo_b);
     const uint32_t ta = (uint32_t)T * a_plane >> 4, tb = (uint32_t)T * b_plane >> 4;
-    for (int ks = 0; ks < ksteps; ++ks)
 #pragma unroll
-        for (int q = 0; q < n_products<T>(); ++q) {
+    for (int i = 0; i < n_products<T>(); ++i) {
+        const int q = product_order<T>(i);
+        for (int ks = 0; ks < ksteps; ++ks) {
             const uint64_t ar = da + (uint32_t)(PI[q] * a_plane + ks * 256) / 16, ai = ar + ta;
             const uint64_t br = db + (uint32_t)(PJ[q] * b_plane + ks * 256) / 16, bi = br + tb;
-            const uint32_t acc = (ks > 0 || q > 0) ? 1u : 0u;
+            const uint32_t acc = (ks > 0 || i > 0) ? 1u : 0u;
             mma_bf16(d_re, ar, br, idesc, acc);
             mma_bf16(d_re, ai, bi, idesc_neg, 1u);
             mma_bf16(d_im, ar, bi, idesc, acc);
             mma_bf16(d_im, ai, br, idesc, 1u);
         }
+    }
 }
 
 // Complex products with the real and imaginary parts side by side in an
@@ -501,15 +581,17 @@ __device__ __forceinline__ void issue_products_cat(uint32_t d0, uint32_t d1, uin
     constexpr int PI[6] = {0, 0, 1, 0, 1, 2}, PJ[6] = {0, 1, 0, 2, 1, 0};
     const uint64_t da = make_desc_sbo(a, sbo_a), db = make_desc_sbo(b, sbo_b);
     const uint32_t ta = (uint32_t)T * a_plane >> 4;
-    for (int ks = 0; ks < ksteps; ++ks)
 #pragma unroll
-        for (int q = 0; q < n_products<T>(); ++q) {
+    for (int i = 0; i < n_products<T>(); ++i) {  // corrections first, hi x hi last (see issue_products)
+        const int q = product_order<T>(i);
+        for (int ks = 0; ks < ksteps; ++ks) {
             const uint64_t ar = da + (uint32_t)(PI[q] * a_plane + ks * 256) / 16, ai = ar + ta;
             const uint64_t bneg = db + (uint32_t)(3 * PJ[q] * b_slot + ks * 256) / 16, bpos = bneg + b_slot / 16;
-            const uint32_t acc = (ks > 0 || q > 0) ? 1u : 0u;
+            const uint32_t acc = (ks > 0 || i > 0) ? 1u : 0u;
             mma_bf16(d0, ar, bpos, idesc, acc);
             mma_bf16(d1, ai, bneg, idesc, d1 == d0 ? 1u : acc);
         }
+    }
 }
 
 __device__ __forceinline__ uint32_t idesc_bf16(int N) {
@@ -939,8 +1021,20 @@ void allow_dyn_smem(const void* kernel, size_t bytes) {
     done.insert({dev, kernel});
 }
 
+// k-tiles (of 32) per chunk of the chunked accumulation (TFMM_TC_CHUNK, default 2,
+// i.e. 4 K steps of 16 per accumulator; 0 turns chunking off).
+int tc_chunk_ktiles() {
+    static const int v = [] {
+        const char* e = std::getenv("TFMM_TC_CHUNK");
+        return e ? std::max(0, std::atoi(e)) : 2;
+    }();
+    return v;
+}
+
 // Ring depth and TMEM columns from the stage's largest K and BN; shared memory is
 // padded so that the CTAs one SM can hold never ask for more than its 512 columns.
+// Stages whose K is longer than one chunk (AG1, AG2, DG1b, DG2, DG3) run the chunked
+// accumulation.
 template <int T, int S>
 void launch_tc(const TcStagePlan& st, const TcCtx& c, cudaStream_t s) {
     if (st.n_tiles == 0) return;
@@ -956,9 +1050,19 @@ void launch_tc(const TcStagePlan& st, const TcCtx& c, cudaStream_t s) {
     constexpr size_t kSmemSM = 228 * 1024, kMaxDyn = 225 * 1024;
     size_t smem = nst * STAGE;
     if (kSmemSM / (smem + 2048) > (size_t)ctas_tmem) smem = std::min(kMaxDyn, kSmemSM / ctas_tmem - 2048);
-    allow_dyn_smem(reinterpret_cast<const void*>(tc_gemm_kernel<T, S>), kMaxDyn);
-    tc_gemm_kernel<T, S><<<st.n_tiles, TTHREADS, smem, s>>>(c, reinterpret_cast<const TcProb*>(st.d_probs), st.d_tiles,
-                                                             nst, tcols, cofs, hsplit);
+    const int chunk = tc_chunk_ktiles();
+    const TcProb* probs = reinterpret_cast<const TcProb*>(st.d_probs);
+    if constexpr (S == TAG1 || S == TAG2 || S == TDG1B || S == TDG2 || S == TDG3) {
+        if (hsplit && chunk > 0 && st.max_kt > chunk) {
+            allow_dyn_smem(reinterpret_cast<const void*>(tc_gemm_kernel<T, S, true>), kMaxDyn);
+            tc_gemm_kernel<T, S, true><<<st.n_tiles, 2 * TTHREADS, smem, s>>>(c, probs, st.d_tiles, nst, tcols, cofs,
+                                                                             hsplit, chunk);
+            TFMM_CUDA_CHECK(cudaGetLastError());
+            return;
+        }
+    }
+    allow_dyn_smem(reinterpret_cast<const void*>(tc_gemm_kernel<T, S, false>), kMaxDyn);
+    tc_gemm_kernel<T, S, false><<<st.n_tiles, TTHREADS, smem, s>>>(c, probs, st.d_tiles, nst, tcols, cofs, hsplit, 1);
     TFMM_CUDA_CHECK(cudaGetLastError());
 }
 

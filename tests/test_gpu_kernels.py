@@ -2,9 +2,17 @@
 
 The factors are seeded synthetic inputs with ragged shapes, given to both sides:
 the oracle applies the Tucker procedures in complex128, the library runs its
-FP32 kernels through the C ABI.  Tolerance: relative l2 error <= 1e-5 per
-output vector (FP32 storage of the factors, ~6e-8 each, and FP32
-accumulation over at most a few thousand terms).
+FP32 kernels through the C ABI.  Tolerance: per output vector (one RHS, group
+and component), relative l2 error <= 1e-5 and every element within 1e-5 of the
+vector's largest magnitude (FP32 storage of the factors, ~6e-8 each, and FP32
+accumulation over at most a few thousand terms).  The element-wise check keeps
+a wrong low-magnitude band (a direction row, the last phi column of an odd
+grid) from hiding under the norm of a long vector.
+
+The split-BF16 tensor-core chain with three terms holds every FP32 operand
+exactly and accumulates in chunks of at most four K steps per TMEM accumulator;
+it is held to the Tucker tolerance gamma = 1e-6 of the many-RHS workload.  Two
+terms keep 16 significant bits per operand and are held to 5e-5.
 """
 import math
 
@@ -68,6 +76,16 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
+def _elem(a, b):
+    """Largest element-wise error relative to the largest reference magnitude."""
+    return float(np.max(np.abs(a - b))) / max(float(np.max(np.abs(b))), 1e-300)
+
+
+def _close(a, b, tol):
+    """Both the relative l2 error and the element-wise error within tol."""
+    return _rel(a, b) <= tol and _elem(a, b) <= tol
+
+
 def test_aggregate_matches_oracle(case):
     tfmm = _tfmm()
     x = complex_gaussian(case["n_rwg"], 11)
@@ -80,7 +98,7 @@ def test_aggregate_matches_oracle(case):
     assert np.isfinite(got).all()
     for g in range(case["G"]):
         for a in range(2):
-            assert _rel(got[g, a], ref[g, a]) <= TOL, (g, a, _rel(got[g, a], ref[g, a]))
+            assert _close(got[g, a], ref[g, a], TOL), (g, a, _rel(got[g, a], ref[g, a]), _elem(got[g, a], ref[g, a]))
 
 
 @pytest.mark.parametrize("weights,beta", [(True, 0.0), (False, 0.0), (True, 0.5 - 0.25j)])
@@ -97,7 +115,7 @@ def test_disaggregate_matches_oracle(case, weights, beta):
     ref = apply.disaggregate_all(case["T"], case["members"], g_in, case["n_rwg"],
                                  case["w"] if weights else None, beta=beta, y0=y0)
     for g, ids in enumerate(case["members"]):
-        assert _rel(got[ids], ref[ids]) <= TOL, (g, _rel(got[ids], ref[ids]))
+        assert _close(got[ids], ref[ids], TOL), (g, _rel(got[ids], ref[ids]), _elem(got[ids], ref[ids]))
 
 
 def test_multi_rhs_and_leading_dimension(case):
@@ -115,9 +133,12 @@ def test_multi_rhs_and_leading_dimension(case):
     Y = yd.cpu().numpy()
     for r in range(R):
         ref = apply.aggregate_all(case["T"], case["members"], X[r, :n])
-        assert _rel(S[r], ref) <= TOL
+        for g in range(case["G"]):
+            for a in range(2):
+                assert _close(S[r, g, a], ref[g, a], TOL), (r, g, a)
         refy = apply.disaggregate_all(case["T"], case["members"], S[r].astype(np.complex128), n, case["w"])
-        assert _rel(Y[r, :n], refy) <= TOL
+        for ids in case["members"]:
+            assert _close(Y[r, ids], refy[ids], TOL), r
         assert np.all(Y[r, n:] == 0)  # padding rows untouched
 
 
@@ -168,9 +189,13 @@ def test_dense_kernels_match_oracle(case):
     torch.cuda.synchronize()
     F = spec.cpu().numpy()[0]
     ref = apply.aggregate_all(tensors, case["members"], x, tucker=False)
-    assert _rel(F, ref) <= TOL
+    for g in range(G):
+        for a in range(2):
+            assert _close(F[g, a], ref[g, a], TOL), (g, a)
     refy = apply.disaggregate_all(tensors, case["members"], F.astype(np.complex128), n, case["w"], tucker=False)
-    assert _rel(yd.cpu().numpy(), refy) <= TOL
+    yg = yd.cpu().numpy()
+    for ids in case["members"]:
+        assert _close(yg[ids], refy[ids], TOL)
 
 
 def test_host_matvec_equals_device_path(case):
@@ -239,13 +264,15 @@ def test_multi_rhs_chain_matches_oracle(name, R):
         ref = apply.aggregate_all(T, members, X[r])
         for g in range(G):
             for a in range(2):
-                assert _rel(S[r, g, a], ref[g, a]) <= TOL, (r, g, a)
+                assert _close(S[r, g, a], ref[g, a], TOL), (r, g, a)
         refy = apply.disaggregate_all(T, members, g_in[r], n_rwg, w, beta=beta, y0=y0[r])
-        assert _rel(Y[r], refy) <= TOL, r
+        for ids in members:
+            assert _close(Y[r, ids], refy[ids], TOL), r
 
 
-@pytest.mark.parametrize("terms,tol", [(3, 1e-5), (2, 5e-5)])
-@pytest.mark.parametrize("name,R", [("paper_like", 16), ("ragged", 7), ("odd_grid", 3), ("wide", 5)])
+@pytest.mark.parametrize("terms,tol", [(3, 1e-6), (2, 5e-5)])
+@pytest.mark.parametrize("name,R", [("paper_like", 16), ("ragged", 7), ("odd_grid", 3), ("wide", 5),
+                                    ("paper_like", 128)])
 def test_tensor_core_chain_matches_oracle(name, R, terms, tol):
     """tcgen05 chains with FP32 operands split into `terms` BF16 terms, FP32 accumulation."""
     tfmm = _tfmm()
@@ -269,10 +296,74 @@ def test_tensor_core_chain_matches_oracle(name, R, terms, tol):
     S = spec.cpu().numpy()
     Y = yd.cpu().numpy()
     assert np.isfinite(S).all() and np.isfinite(Y).all()
+    worst = [0.0, 0.0]
     for r in range(R):
         ref = apply.aggregate_all(T, members, X[r])
         for g in range(G):
             for a in range(2):
-                assert _rel(S[r, g, a], ref[g, a]) <= tol, (r, g, a, _rel(S[r, g, a], ref[g, a]))
+                e = (_rel(S[r, g, a], ref[g, a]), _elem(S[r, g, a], ref[g, a]))
+                worst[0] = max(worst[0], *e)
+                assert max(e) <= tol, (r, g, a, e)
         refy = apply.disaggregate_all(T, members, g_in[r], n_rwg, w, beta=beta, y0=y0[r])
-        assert _rel(Y[r], refy) <= tol, (r, _rel(Y[r], refy))
+        for ids in members:
+            e = (_rel(Y[r, ids], refy[ids]), _elem(Y[r, ids], refy[ids]))
+            worst[1] = max(worst[1], *e)
+            assert max(e) <= tol, (r, e)
+    print(f"{name} R={R} terms={terms}: worst aggregation {worst[0]:.2e}, disaggregation {worst[1]:.2e}")
+
+
+def test_tensor_core_chain_on_far_field_factors():
+    """The 3-term tensor-core chain on the oracle's own T-HOSVD factors of real far-field
+    tensors (orthonormal factors, paper-shaped ranks): 10-lambda sphere, 1-lambda boxes,
+    6 digits (26 x 52 directions), gamma = 1e-6, four groups at size quantiles, 128 RHS.
+    Every (RHS, group, component) spectrum and every group's currents within gamma of the
+    oracle's Tucker procedures with the same factors, in l2 and element-wise."""
+    import oracle
+    from paper_2103_05822_gb300.inputs import WORKLOADS, icosphere
+    tfmm = _tfmm()
+    w = WORKLOADS["sphere10"]
+    v, f = icosphere(w.diameter, w.nu)
+    P0 = oracle.problem.build(v, f, k=2 * math.pi, box=w.box, digits=w.digits, tol=w.tol,
+                              compress=False, keep_tensors=False)
+    sizes = np.array([len(m) for m in P0.groups.members])
+    order = np.argsort(sizes, kind="stable")
+    pick = sorted({int(order[i]) for i in np.linspace(0, len(order) - 1, 4).round().astype(int)})
+    P = oracle.problem.build(v, f, k=2 * math.pi, box=w.box, digits=w.digits, tol=w.tol,
+                             compress=True, keep_tensors=False, groups_subset=pick)
+    # the picked groups' RWGs renumbered 0..n-1
+    members, pos = [], 0
+    for g in pick:
+        members.append(np.arange(pos, pos + len(P.groups.members[g])))
+        pos += len(P.groups.members[g])
+    T = [P.tucker[g] for g in pick]
+    factors = [[(t.U_theta, t.U_phi, t.U_beta, t.core) for t in per] for per in T]
+    nt, npf = P.grid.n_theta, P.grid.n_phi
+    R, G, nd = 128, len(pick), nt * npf
+    plan = tfmm.tfmm_plan_from_tucker(pos, nt, npf, members, factors, weights=P.grid.weights, max_rhs=R,
+                                      mrhs_precision=3)
+    X = complex_gaussian((R, pos), 31)
+    gin = complex_gaussian((R, G, 2, nd), 32)
+    xd = torch.from_numpy(X.astype(np.complex64)).cuda()
+    spec = torch.full((R, G, 2, nd), float("nan"), dtype=torch.complex64, device="cuda")
+    tfmm.tfmm_aggregate(plan, xd, spec)
+    gd = torch.from_numpy(gin.astype(np.complex64)).cuda()
+    yd = torch.full((R, pos), float("nan"), dtype=torch.complex64, device="cuda")
+    tfmm.tfmm_disaggregate(plan, gd, yd)
+    torch.cuda.synchronize()
+    assert plan.info["kernel_errors"] == 0
+    S, Y = spec.cpu().numpy(), yd.cpu().numpy()
+    gamma = w.tol
+    worst = [0.0, 0.0]
+    for r in range(R):
+        ref = apply.aggregate_all(T, members, X[r])
+        refy = apply.disaggregate_all(T, members, gin[r], pos, P.grid.weights)
+        for k in range(G):
+            for a in range(2):
+                e = max(_rel(S[r, k, a], ref[k, a]), _elem(S[r, k, a], ref[k, a]))
+                worst[0] = max(worst[0], e)
+                assert e <= gamma, (r, pick[k], a, e)
+            ids = members[k]
+            e = max(_rel(Y[r, ids], refy[ids]), _elem(Y[r, ids], refy[ids]))
+            worst[1] = max(worst[1], e)
+            assert e <= gamma, (r, pick[k], e)
+    print(f"far-field factors, groups {pick}: worst aggregation {worst[0]:.2e}, disaggregation {worst[1]:.2e}")
