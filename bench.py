@@ -47,14 +47,19 @@ def parse():
     ap.add_argument("--workload", default="sphere30")
     ap.add_argument("--no-dense", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--oracle-groups", type=int, default=3)
-    ap.add_argument("--graph", action="store_true", help="replay one captured CUDA graph per step")
+    ap.add_argument("--oracle-groups", type=int, default=5)
+    ap.add_argument("--graph", dest="graph", action="store_true", default=True,
+                    help="replay one captured CUDA graph of the two stages per step (default)")
+    ap.add_argument("--no-graph", dest="graph", action="store_false", help="launch the two stages eagerly per step")
     ap.add_argument("--sweep", action="store_true",
                     help="parameter sweep on the 20-lambda sphere (box x tolerance x digits, 16 RHS): "
                          "one JSON line per point")
     ap.add_argument("--sweep-boxes", default="0.5,1,2,4")
     ap.add_argument("--sweep-tols", default="1e-3,1e-4,1e-6,1e-8")
     ap.add_argument("--sweep-digits", default="3,6")
+    ap.add_argument("--svd", action="store_true",
+                    help="also build the truncated-SVD comparator (Sec. II.C) of the workload and time it: "
+                         "the Table III analogue (dense / SVD / Tucker memory and ms) on one GPU")
     ap.add_argument("--mrhs-precision", type=int, default=None,
                     help="R > 1: 0 FP32 CUDA cores, 2 / 3 tensor cores with 2- / 3-term split BF16 (default 3)")
     return ap.parse_args()
@@ -83,12 +88,19 @@ def whole_job_ms(total_ms, steps, world, device=None):
 
 
 def workload_desc(w, L=None, n_theta=None, n_phi=None, G=None):
-    d = (f"PEC sphere D={w.diameter:g} lambda, icosphere nu={w.nu} ({w.n_tri} triangles, {w.n_rwg} RWGs), "
-         f"{w.box:g}-lambda boxes, d0={w.digits} digits")
+    if w.shape == "trihedral":
+        d = (f"PEC square trihedral corner reflector, {w.diameter:g}-lambda plates, {w.nu}x{w.nu} squares per plate "
+             f"({w.n_tri} triangles, {w.n_rwg} RWGs), {w.box:g}-lambda boxes, d0={w.digits} digits")
+    else:
+        d = (f"PEC sphere D={w.diameter:g} lambda, icosphere nu={w.nu} ({w.n_tri} triangles, {w.n_rwg} RWGs), "
+             f"{w.box:g}-lambda boxes, d0={w.digits} digits")
     if L is not None:
         d += f" (L={L}, {n_theta}x{n_phi} directions, {G} groups)"
     if w.rhs == "planewave_sweep":
         d += f", Tucker tol {w.tol:g}, {w.nrhs} RWG-tested plane waves theta_inc = pi i/{w.nrhs - 1}, phi_inc = 0, theta-polarised"
+    elif w.rhs == "planewave_corner":
+        d += (f", N_phi = 2L+1, Tucker tol {w.tol:g}, RWG-tested plane wave theta_inc = 135 deg, phi_inc = 225 deg, "
+              f"theta-polarised")
     else:
         d += f", Tucker tol {w.tol:g}, {w.nrhs} RHS CN(0,1) seed {w.seed}"
     return d
@@ -161,13 +173,23 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------- cpu baseline
+def size_quantile_groups(sizes, count):
+    """Group ids at evenly spaced quantiles of the group size (smallest and largest included)."""
+    order = np.argsort(np.asarray(sizes), kind="stable")
+    q = np.linspace(0, len(order) - 1, max(count, 1)).round().astype(int)
+    return sorted({int(order[i]) for i in q})
+
+
 def oracle_sample(w, verts, tris, n_groups_sample, seed):
-    """Oracle far-fields + T-HOSVD for a few groups of the workload (setup, untimed)."""
+    """Oracle far-fields + T-HOSVD for a few groups of the workload (setup, untimed).
+
+    The groups sit at evenly spaced quantiles of the group size, so that the
+    per-group times span the whole size range the scaling below extrapolates over.
+    """
     import oracle
     P = oracle.problem.build(verts, tris, k=2 * math.pi, box=w.box, digits=w.digits, tol=w.tol,
-                             compress=False, keep_tensors=False)
-    G = P.groups.n_groups
-    pick = sorted(set(int(round(i * (G - 1) / max(n_groups_sample - 1, 1))) for i in range(n_groups_sample)))
+                             nphi_rule="2L+1" if w.nphi_rule == 0 else "2L+2", compress=False, keep_tensors=False)
+    pick = size_quantile_groups([len(m) for m in P.groups.members], n_groups_sample)
     tuck, dense = {}, {}
     for g in pick:
         At, Ap = P.group_tensors(g)
@@ -177,35 +199,54 @@ def oracle_sample(w, verts, tris, n_groups_sample, seed):
     return P, pick, tuck, dense
 
 
-def oracle_step(P, pick, tuck, x):
-    """Oracle Tucker aggregation + disaggregation of the sampled groups (complex128)."""
+def oracle_group_step(P, g, tuck, x):
+    """Oracle Tucker aggregation + disaggregation of one group (complex128)."""
     from oracle import apply
-    for g in pick:
-        ids = P.groups.members[g]
-        xg = x[ids]
-        F = [apply.tucker_aggregate(tuck[g][a], xg) for a in range(2)]
-        y = sum(apply.tucker_disaggregate(tuck[g][a], F[a], P.grid.weights) for a in range(2))
-    return y
+    xg = x[P.groups.members[g]]
+    F = [apply.tucker_aggregate(tuck[g][a], xg) for a in range(2)]
+    return sum(apply.tucker_disaggregate(tuck[g][a], F[a], P.grid.weights) for a in range(2))
+
+
+def scale_group_times(sizes_sample, times_sample, sizes_all):
+    """Whole-problem time from per-group times of a size-quantile sample.
+
+    Fits t = a + b n_beta by least squares over the sampled groups (the oracle's
+    cost per group is affine in its size: the n_beta r_beta terms grow with n_beta,
+    the core and angular terms do not) and sums the fit over every group.  Falls
+    back to scaling by the groups' share of RWGs when the fit is degenerate.
+    """
+    n = np.asarray(sizes_sample, float)
+    t = np.asarray(times_sample, float)
+    N = np.asarray(sizes_all, float)
+    if len(set(n.tolist())) >= 2:
+        b, a = np.polyfit(n, t, 1)
+        pred = a + b * N
+        if np.all(pred > 0):
+            return float(pred.sum())
+    return float(t.sum() * N.sum() / n.sum())
 
 
 def time_oracle(P, pick, tuck, x, steps, warmup, budget_s=None):
+    """ms per whole-problem Tucker agg + disagg, extrapolated from the sampled groups."""
     for _ in range(warmup):
-        oracle_step(P, pick, tuck, x)
-    t = []
+        for g in pick:
+            oracle_group_step(P, g, tuck, x)
+    per = {g: [] for g in pick}
     n = 0
     t0 = time.perf_counter()
     while True:
-        s = time.perf_counter()
-        oracle_step(P, pick, tuck, x)
-        t.append(time.perf_counter() - s)
+        for g in pick:
+            s = time.perf_counter()
+            oracle_group_step(P, g, tuck, x)
+            per[g].append(time.perf_counter() - s)
         n += 1
         if budget_s is None and n >= steps:
             break
         if budget_s is not None and (time.perf_counter() - t0 >= budget_s and n >= 3):
             break
-    G = P.groups.n_groups
-    # scale the sampled groups to the whole problem by their share of Tucker work
-    return 1e3 * statistics.median(t) * G / len(pick), n
+    sizes = [len(m) for m in P.groups.members]
+    total_s = scale_group_times([sizes[g] for g in pick], [statistics.median(per[g]) for g in pick], sizes)
+    return 1e3 * total_s, n
 
 
 def cpu_threads():
@@ -223,15 +264,16 @@ def cpu_threads():
 def run_reference(args, w, world, rank):
     if rank != 0:
         return
-    from paper_2103_05822_gb300.inputs import complex_gaussian, icosphere
-    verts, tris = icosphere(w.diameter, w.nu)
+    from paper_2103_05822_gb300.inputs import complex_gaussian, workload_mesh
+    verts, tris = workload_mesh(w)
     P, pick, tuck, _ = oracle_sample(w, verts, tris, args.oracle_groups, w.seed)
     R = w.nrhs
     x = complex_gaussian((P.n_rwg, R) if R > 1 else P.n_rwg, w.seed)  # timing does not depend on the values
     ms, n = time_oracle(P, pick, tuck, x, args.steps, args.warmup)
     cores = cpu_threads()
-    sample = (f"{len(pick)} of {P.groups.n_groups} groups (oracle far-field + T-HOSVD untimed); "
-              f"median of {n} steps of Tucker agg+disagg of {R} column(s) on them, scaled by groups to the whole sphere")
+    sample = (f"{len(pick)} of {P.groups.n_groups} groups at size quantiles (oracle far-field + T-HOSVD untimed); "
+              f"median of {n} timings per group of Tucker agg+disagg of {R} column(s), extrapolated to every "
+              f"group by a least-squares fit of time vs group size")
     line = {
         "impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
@@ -265,7 +307,7 @@ def traffic_record(kernel, factor_bytes):
 def run_ours(args, w, world, rank, local):
     import torch
     from paper_2103_05822_gb300 import tfmm
-    from paper_2103_05822_gb300.inputs import complex_gaussian, icosphere
+    from paper_2103_05822_gb300.inputs import complex_gaussian, workload_mesh
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -280,11 +322,11 @@ def run_ours(args, w, world, rank, local):
 
     R = w.nrhs
     use_dense = not args.no_dense and R <= 8  # the dense comparator streams 16 N N_dir bytes per column
-    verts, tris = icosphere(w.diameter, w.nu)
+    verts, tris = workload_mesh(w)
     t0 = time.perf_counter()
     mesh = tfmm.tfmm_mesh_create(verts, tris)
     mp = args.mrhs_precision if args.mrhs_precision is not None else (3 if R > 1 else 0)
-    prm = tfmm.tfmm_params_default(k=2 * math.pi, box=w.box, digits=float(w.digits), tol=w.tol,
+    prm = tfmm.tfmm_params_default(k=2 * math.pi, box=w.box, digits=float(w.digits), tol=w.tol, nphi_rule=w.nphi_rule,
                                    keep_dense=1 if use_dense else 0, max_rhs=R, mrhs_precision=mp)
     stream = torch.cuda.current_stream()
     plan = tfmm.tfmm_plan_create(mesh, prm, stream=stream)
@@ -300,6 +342,15 @@ def run_ours(args, w, world, rank, local):
         tfmm.tfmm_planewave(plan, kh, pol, xv, stream=stream)
         torch.cuda.synchronize()
         x_host = xv.cpu().numpy()
+    elif w.rhs == "planewave_corner":
+        # Sec. III.A: k_inc at theta = 135 deg, phi = 225 deg, theta-polarised
+        th, ph = math.radians(135.0), math.radians(225.0)
+        kh = np.array([[math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)]])
+        pol = np.array([[math.cos(th) * math.cos(ph), math.cos(th) * math.sin(ph), -math.sin(th)]])
+        xv = torch.empty((1, N), dtype=torch.complex64, device=dev)
+        tfmm.tfmm_planewave(plan, kh, pol, xv, stream=stream)
+        torch.cuda.synchronize()
+        x_host = xv.cpu().numpy().reshape(N)
     else:
         x_host = complex_gaussian((R, N) if R > 1 else N, w.seed).astype(np.complex64)
     x = torch.from_numpy(x_host).to(dev)
@@ -412,6 +463,43 @@ def run_ours(args, w, world, rank, local):
         torch.cuda.synchronize()
         rel = float(torch.linalg.vector_norm(spec - ref) / torch.linalg.vector_norm(ref))
 
+    svd_rec = None
+    if args.svd:
+        # the same workload compressed by the truncated SVD of each aggregation matrix at gamma
+        t1 = time.perf_counter()
+        prm_s = tfmm.tfmm_params_default(k=2 * math.pi, box=w.box, digits=float(w.digits), tol=w.tol,
+                                         nphi_rule=w.nphi_rule, keep_dense=0, max_rhs=R, compression=tfmm.SVD)
+        plan_s = tfmm.tfmm_plan_create(mesh, prm_s, stream=stream)
+        setup_svd = time.perf_counter() - t1
+        spec_s = torch.empty_like(spec)
+
+        def step_svd(ev=None):
+            if ev is not None:
+                ev[0].record(stream)
+            tfmm.tfmm_aggregate(plan_s, x, spec_s, stream=stream)
+            if ev is not None:
+                ev[1].record(stream)
+            tfmm.tfmm_disaggregate(plan_s, spec_s, y, stream=stream)
+            if ev is not None:
+                ev[2].record(stream)
+
+        stot, sagg, sdis = timed(step_svd, args.steps, args.warmup)
+        info_s = plan_s.info
+        rel_s = None
+        if dense is not None:
+            ref = torch.empty_like(spec)
+            tfmm.tfmm_aggregate(plan_s, x, spec_s, stream=stream)
+            tfmm.tfmm_aggregate_dense(plan, x, ref, stream=stream)
+            torch.cuda.synchronize()
+            rel_s = float(torch.linalg.vector_norm(spec_s - ref) / torch.linalg.vector_norm(ref))
+        sb = info_s["tucker_bytes_alg"]
+        svd_rec = {"ms_per_matvec": stot / args.steps, "aggregate_ms": statistics.mean(sagg),
+                   "disaggregate_ms": statistics.mean(sdis), "bytes": sb, "compression": 8 * 2 * N * nd / sb,
+                   "aggregate_gbs": (sb + 8 * N * R + 16 * G * nd * R) / statistics.mean(sagg) / 1e6,
+                   "max_rank_beta": info_s["max_rank"][2], "rel_err_vs_dense_gpu": rel_s, "setup_s": setup_svd}
+        del plan_s, spec_s
+        torch.cuda.empty_cache()
+
     # roofline of the dominant kernel (algorithmic bytes or flops per launch / mean launch time)
     fac = info["tucker_bytes_alg"]
     bytes_agg = fac + 8 * N * R + 16 * G * nd * R
@@ -487,8 +575,9 @@ def run_ours(args, w, world, rank, local):
                       "what": "aggregation spectra vs the oracle's FP64 far-fields and dense Eq. 3"}
         ms_cpu, n = time_oracle(P, pick, tuck, xo, 0, 1, budget_s=10.0)
         cpu = {"value": ms_cpu, "unit": "ms", "cores": cpu_threads(), "kind": "oracle",
-               "sample": f"{len(pick)} of {G} groups, oracle Tucker agg+disagg (complex128) timed {n} times "
-                         f"(~10 s), median scaled by groups to the whole sphere; oracle setup untimed"}
+               "sample": f"{len(pick)} of {G} groups at size quantiles, oracle Tucker agg+disagg (complex128) "
+                         f"timed {n} times per group (~10 s), extrapolated to every group by a least-squares "
+                         f"fit of time vs group size; oracle setup untimed"}
 
     if rank == 0:
         line = {
@@ -496,12 +585,15 @@ def run_ours(args, w, world, rank, local):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "complex64", "data": "synthetic",
             "config": {"workload": workload_desc(w, info["L"], info["n_theta"], info["n_phi"], G),
-                       "l2": "no flush: Tucker factors ({:.2f} GB) exceed the 129 MB L2".format(fac / 1e9),
+                       "l2": ("no flush: Tucker factors ({:.2f} GB) exceed the 129 MB L2".format(fac / 1e9) if fac > 129e6
+                              else "Tucker factors ({:.3f} GB) fit in the 129 MB L2: no flush, timings are "
+                                   "L2-resident".format(fac / 1e9)),
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "stages": {"aggregate_ms": agg_ms, "disaggregate_ms": dis_ms,
                        "aggregate_gbs": bytes_agg / agg_ms / 1e6, "disaggregate_gbs": bytes_dis / dis_ms / 1e6},
             "dense": dense,
             "speedup_vs_dense": (dense["ms_per_matvec"] / ms_step) if dense else None,
+            "svd": svd_rec,
             "rel_err_vs_dense_gpu": rel, "rel_err_vs_oracle": err_oracle,
             "memory": {"tucker_bytes": info["tucker_bytes"], "tucker_bytes_alg": fac,
                        "dense_bytes": 8 * 2 * N * nd, "compression": 8 * 2 * N * nd / fac,

@@ -41,3 +41,36 @@ def test_workload_text_names_the_sizes():
     txt = bench.workload_desc(WORKLOADS["sphere30"], 39, 40, 80, 1034)
     for part in ("30 lambda", "972000 RWGs", "40x80", "1034 groups", "1e-06"):
         assert part in txt, (part, txt)
+
+
+def test_default_run_replays_a_cuda_graph():
+    import sys
+    old = sys.argv
+    try:
+        sys.argv = ["bench.py"]
+        assert bench.parse().graph is True
+        sys.argv = ["bench.py", "--no-graph"]
+        assert bench.parse().graph is False
+    finally:
+        sys.argv = old
+
+
+def test_size_quantile_groups_span_the_size_range():
+    sizes = [50, 900, 10, 1786, 400, 940, 30]
+    pick = bench.size_quantile_groups(sizes, 5)
+    assert 2 in pick and 3 in pick  # the smallest and the largest group
+    assert len(pick) == 5 and pick == sorted(pick)
+
+
+def test_group_time_extrapolation_is_exact_for_an_affine_cost():
+    """Per-group times t = a + b n_beta: the fit over a sample reproduces the total exactly,
+    where plain scaling by the group count would be biased by the sample's sizes."""
+    import numpy as np
+    rng = np.random.default_rng(3)
+    sizes = rng.integers(20, 1800, 500)
+    a, b = 2e-4, 1e-6
+    pick = bench.size_quantile_groups(sizes, 5)
+    total = bench.scale_group_times(sizes[pick], a + b * sizes[pick], sizes)
+    assert abs(total - float(np.sum(a + b * sizes))) <= 1e-9 * total
+    # a degenerate sample (one size) falls back to the groups' share of RWGs
+    assert abs(bench.scale_group_times([100, 100], [1.0, 1.0], [100, 300]) - 4.0) < 1e-12
