@@ -17,8 +17,11 @@ Everything is plain NumPy in complex128 / float64, written from the paper:
                  and the Tucker procedures of Figs. 2b and 3b.
 * ``planewave``- the RWG-tested plane-wave excitation V_m of Eq. 2.
 * ``memory``   - far-field storage of the dense and the Tucker format.
+* ``svd``      - the truncated-SVD comparator of Sec. II.C (ref. [11]).
+* ``translation`` - the FMM translation stage between aggregation and
+                 disaggregation (addition theorem, ref. [25]), by direct sums.
 
 Every function is pinned by ``tests/test_oracle_*.py`` to something other than
 itself (closed forms, brute force, invariants, the paper's printed numbers).
 """
-from . import rwg, grid, groups, farfield, hosvd, apply, planewave, memory, problem  # noqa: F401
+from . import rwg, grid, groups, farfield, hosvd, apply, planewave, memory, problem, svd, translation  # noqa: F401

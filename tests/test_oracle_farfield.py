@@ -15,7 +15,7 @@ import pytest
 from scipy import special
 
 import oracle
-from oracle import farfield, grid, planewave, rwg
+from oracle import farfield, grid, planewave, rwg, translation
 
 
 def _divdiff_exp(nodes):
@@ -140,17 +140,6 @@ def _direct_efie(verts, tris, r, m, n, k, order=7):
     return total
 
 
-def _translation(L, k, X, khat):
-    """T_L(k_hat, X) = sum_l (-j)^l (2l+1) h_l^(2)(k|X|) P_l(k_hat . X_hat), ref. [25]."""
-    x = k * np.linalg.norm(X)
-    c = khat @ (X / np.linalg.norm(X))
-    T = np.zeros(len(khat), complex)
-    for l in range(L + 1):
-        h2 = special.spherical_jn(l, x) - 1j * special.spherical_yn(l, x)
-        T += (-1j) ** l * (2 * l + 1) * h2 * special.eval_legendre(l, c)
-    return T
-
-
 @pytest.mark.parametrize("digits", [4, 6])
 def test_two_group_translation_matches_direct_interaction(digits):
     k = 2 * math.pi
@@ -179,7 +168,7 @@ def test_two_group_translation_matches_direct_interaction(digits):
         for ahat in (g.theta_hat, g.phi_hat):
             Pm = np.einsum("ci,ic->i", Jm, ahat)
             Pn = np.einsum("ci,ic->i", Jn, ahat)
-            Z_fmm = Z_fmm + np.sum(g.weights * _translation(L, k, X, g.khat) * np.conj(Pm) * Pn)
+            Z_fmm = Z_fmm + np.sum(g.weights * translation.translation_operator(L, k, X, g.khat) * np.conj(Pm) * Pn)
         Z_fmm *= -1j * k / (16 * math.pi ** 2)
         Z_dir = _direct_efie(verts, tris, r, m, n, k)
         worst = max(worst, abs(Z_fmm - Z_dir) / abs(Z_dir))
