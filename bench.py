@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--sweep-boxes", default="0.5,1,2,4")
     ap.add_argument("--sweep-tols", default="1e-3,1e-4,1e-6,1e-8")
     ap.add_argument("--sweep-digits", default="3,6")
+    ap.add_argument("--translate", action="store_true",
+                    help="also time the translation stage (FMM-FFT, tfmm_translate) between the two stages and "
+                         "report the far-field matvec aggregate -> translate -> disaggregate")
     ap.add_argument("--svd", action="store_true",
                     help="also build the truncated-SVD comparator (Sec. II.C) of the workload and time it: "
                          "the Table III analogue (dense / SVD / Tucker memory and ms) on one GPU")
@@ -463,6 +466,31 @@ def run_ours(args, w, world, rank, local):
         torch.cuda.synchronize()
         rel = float(torch.linalg.vector_norm(spec - ref) / torch.linalg.vector_norm(ref))
 
+    trans_rec = None
+    if args.translate:
+        spec_in = torch.empty_like(spec)
+        t1 = time.perf_counter()
+        tfmm.tfmm_translate(plan, spec, spec_in, stream=stream)  # first call builds the transform of T_L
+        torch.cuda.synchronize()
+        build_s = time.perf_counter() - t1
+
+        def step_far(ev=None):
+            if ev is not None:
+                ev[0].record(stream)
+            tfmm.tfmm_aggregate(plan, x, spec, stream=stream)
+            tfmm.tfmm_translate(plan, spec, spec_in, stream=stream)
+            if ev is not None:
+                ev[1].record(stream)
+            tfmm.tfmm_disaggregate(plan, spec_in, y, stream=stream)
+            if ev is not None:
+                ev[2].record(stream)
+
+        ftot, fa, fd = timed(step_far, args.steps, args.warmup)
+        trans_rec = {"far_matvec_ms": ftot / args.steps, "aggregate_plus_translate_ms": statistics.mean(fa),
+                     "disaggregate_ms": statistics.mean(fd), "build_s": build_s}
+        trans_rec["translate_ms"] = trans_rec["aggregate_plus_translate_ms"] - statistics.mean(agg)
+        del spec_in
+
     svd_rec = None
     if args.svd:
         # the same workload compressed by the truncated SVD of each aggregation matrix at gamma
@@ -594,6 +622,7 @@ def run_ours(args, w, world, rank, local):
             "dense": dense,
             "speedup_vs_dense": (dense["ms_per_matvec"] / ms_step) if dense else None,
             "svd": svd_rec,
+            "translation": trans_rec,
             "rel_err_vs_dense_gpu": rel, "rel_err_vs_oracle": err_oracle,
             "memory": {"tucker_bytes": info["tucker_bytes"], "tucker_bytes_alg": fac,
                        "dense_bytes": 8 * 2 * N * nd, "compression": 8 * 2 * N * nd / fac,

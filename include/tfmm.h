@@ -235,6 +235,27 @@ tfmm_status tfmm_disaggregate_dense(tfmm_plan* plan, const tfmm_cfloat* spectra,
 tfmm_status tfmm_matvec_host(tfmm_plan* plan, const tfmm_cfloat* x_host, tfmm_cfloat* y_host, int32_t R,
                              int32_t dense, void* stream);
 
+/* Translation stage of the FMM-FFT (Sec. II.A, between Eqs. 3 and 5; refs. [7, 8];
+ * addition theorem of ref. [25]): the incoming spectra of every group from the
+ * outgoing spectra of aggregation,
+ *   spectra_in[r][v][alpha](k_i) = (-j k / (16 pi^2)) sum over groups v' far from v of
+ *                                  T_L(k_i, r_v - r_v') spectra_out[r][v'][alpha](k_i),
+ *   T_L(k, X) = sum_{l=0}^{L} (-j)^l (2l + 1) h_l^(2)(k|X|) P_l(k . X / |X|),
+ * where two groups are far when their box indices differ by 2 or more in some
+ * coordinate (touching boxes are the near field, not computed here).  Then
+ * tfmm_disaggregate(spectra_in, apply_weights = 1) gives the far part of Z x of the
+ * EFIE (Eq. 2) for the x that tfmm_aggregate received.  Evaluated as a 3-D FFT
+ * convolution over the zero-padded box grid, FP32 (the translation kernel's
+ * transform is computed once in FP64).  The first call builds it (device memory
+ * owned by the plan: the kernel's transform, N_grid x N_dir complex, and a work
+ * grid of N_grid x 2 N_dir complex, N_grid >= (2K_x - 1)(2K_y - 1)(2K_z - 1));
+ * later calls allocate nothing.
+ *   spectra_out  device, R x G x 2 x N_dir FP32 complex (as tfmm_aggregate writes it)
+ *   spectra_in   device, same shape, overwritten; must not alias spectra_out
+ * Errors: INVALID_ARG (a plan built from factors has no box geometry), OOM, CUDA. */
+tfmm_status tfmm_translate(tfmm_plan* plan, const tfmm_cfloat* spectra_out, int32_t R, tfmm_cfloat* spectra_in,
+                           void* stream);
+
 /* RWG-tested plane-wave excitations (Eq. 2): V[m + n_rwg r] =
  * -int b_m(r') . pol_r exp(-j k khat_r . r') dr' for R incidences.
  *   khat, pol  host, R x 3 (row-major) propagation directions and polarisations
@@ -322,7 +343,9 @@ typedef struct {
                                        AG3+AG4 kernel, 0 or 16..256 (0: the largest that fits) */
     int32_t tc_dg1a_pairs;          /* tensor cores: (i_phi, r) pairs per CTA of DG1a, 0, 64 or 128
                                        (0: 128 when it fits, else 64) */
-    int32_t reserved[1];
+    int32_t single_rhs_split;       /* single-RHS stages as three launches that spread every work
+                                       item over many CTAs (for plans with few, large groups):
+                                       0 automatic (fewer work items than 2 x SMs), 1 always, 2 never */
     double agg_ms, dis_ms;          /* times the autotuner measured (0 if not tuned) */
 } tfmm_tuning;
 tfmm_status tfmm_plan_tuning_get(const tfmm_plan* plan, tfmm_tuning* t);
@@ -339,6 +362,13 @@ tfmm_status tfmm_plan_tuning_set(tfmm_plan* plan, const tfmm_tuning* t, void* st
  * chosen tuning.  No counterpart in the paper. */
 tfmm_status tfmm_autotune(tfmm_plan* plan, int32_t R, double budget_ms, int32_t allow_two_term, void* stream,
                           tfmm_tuning* out);
+
+/* Test hook for the error paths (no counterpart in the paper): the nth device
+ * allocation the library makes from now on, on any thread, fails as if the device
+ * were out of memory, so the call that makes it returns TFMM_OOM; 0 disarms it.
+ * Every plan resource is owned by the plan or by a scoped buffer, so a failed call
+ * leaves no device memory behind.  Errors: INVALID_ARG for nth < 0. */
+tfmm_status tfmm_test_fail_allocation(int64_t nth);
 
 #ifdef __cplusplus
 }

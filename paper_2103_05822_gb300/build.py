@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libtfmm.so")
 
-SOURCES = ["tfmm_host.cpp", "runtime.cpp", "setup.cu", "apply.cu", "mrhs.cu", "mrhs_tc.cu"]
+SOURCES = ["tfmm_host.cpp", "runtime.cpp", "setup.cu", "apply.cu", "mrhs.cu", "mrhs_tc.cu", "translate.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off", "-Xptxas", "-v"]
 
@@ -51,7 +51,7 @@ def build(verbose: bool = False) -> str:
             sys.stderr.write(f"--- {os.path.basename(obj)}\n{log}")
     objs = [o for o, _ in results]
     tmp = LIB + ".tmp"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcublas", "-lcusolver", "-lcudart"]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcublas", "-lcusolver", "-lcufft", "-lcudart"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stderr}")

@@ -36,6 +36,8 @@ __device__ __forceinline__ float4 ld_stream(const float4* p) {
     return v;
 }
 
+__host__ __device__ __forceinline__ int64_t round_up_dev(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
 // acc += a * b (complex)
 __device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
     acc.x = fmaf(a.x, b.x, acc.x);
@@ -163,6 +165,45 @@ __device__ __forceinline__ void rowaxpy(const float4* __restrict__ M, int ld2, i
     }
 }
 
+// C(m, n) = sum_{k < K} A(m, k) B(k, n) for the small theta / phi contractions, all
+// operands in shared memory: every thread computes a TM x TN block of outputs in
+// registers, so a complex multiply-add costs (TM + TN) / (TM TN) shared-memory loads
+// instead of two.  a(m, k) and b(k, n) read the operands (indices clamped to the
+// valid range); emit(m, n, v) stores one result.
+template <int TM, int TN, class LA, class LB, class Emit>
+__device__ __forceinline__ void smem_gemm(int M, int N, int K, LA a, LB b, Emit emit) {
+    const int mt = (M + TM - 1) / TM, nt = (N + TN - 1) / TN;
+    for (int t = threadIdx.x; t < mt * nt; t += blockDim.x) {
+        const int m0 = (t % mt) * TM, n0 = (t / mt) * TN;
+        float2 acc[TM][TN];
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) acc[i][j] = make_float2(0.f, 0.f);
+        int mi[TM], nj[TN];
+#pragma unroll
+        for (int i = 0; i < TM; ++i) mi[i] = min(m0 + i, M - 1);
+#pragma unroll
+        for (int j = 0; j < TN; ++j) nj[j] = min(n0 + j, N - 1);
+        for (int k = 0; k < K; ++k) {
+            float2 av[TM], bv[TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) av[i] = a(mi[i], k);
+#pragma unroll
+            for (int j = 0; j < TN; ++j) bv[j] = b(k, nj[j]);
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) cfma(acc[i][j], av[i], bv[j]);
+        }
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j)
+                if (m0 + i < M && n0 + j < N) emit(m0 + i, n0 + j, acc[i][j]);
+    }
+}
+
 struct SmemLayout {  // offsets in float2 units, each 16-byte aligned
     int o_a, o_b, o_c, o_d, o_e, o_f, o_g, o_h, total;
     int ldt, ldp, ldv, ldg;
@@ -188,7 +229,7 @@ struct AggArgs {
 // format with identity theta / phi factors, core C_(3) = (U Sigma)^T and U_beta =
 // conj(V): the spectrum is AG1 followed by AG2 written straight to it.
 template <bool SVD>
-__global__ void __launch_bounds__(512) tucker_aggregate_kernel(const AggArgs a) {
+__global__ void __launch_bounds__(512, 3) tucker_aggregate_kernel(const AggArgs a) {
     extern __shared__ float4 smem4[];
     float2* sm = reinterpret_cast<float2*>(smem4);
     __shared__ int s_item;
@@ -240,20 +281,20 @@ __global__ void __launch_bounds__(512) tucker_aggregate_kernel(const AggArgs a) 
                     [&](int j, float4 v) { reinterpret_cast<float4*>(s_M)[j] = v; });
             __syncthreads();
             // AG3: V[i_phi, a] = sum_b U_phi[i_phi, b] M[a, b]
-            for (int o = tid; o < a.n_phi * d.rt; o += NT) {
-                const int ip = o % a.n_phi, aa = o / a.n_phi;
-                float2 acc = make_float2(0.f, 0.f);
-                for (int b = 0; b < d.rp; ++b) cfma(acc, s_up[ip + a.L.ldp * b], s_M[aa + d.rt * b]);
-                s_V[ip + a.L.ldv * aa] = acc;
+            {
+                const int ldp = a.L.ldp, ldv = a.L.ldv, rt = d.rt;
+                smem_gemm<2, 2>(a.n_phi, rt, d.rp, [&](int ip, int b) { return s_up[ip + ldp * b]; },
+                                [&](int b, int aa) { return s_M[aa + rt * b]; },
+                                [&](int ip, int aa, float2 v) { s_V[ip + ldv * aa] = v; });
             }
             __syncthreads();
             // AG4: F[i_theta, i_phi] = sum_a U_theta[i_theta, a] V[i_phi, a]
-            float2* out = a.spec + (((int64_t)r * a.G + d.g) * 2 + d.alpha) * a.n_dir;
-            for (int o = tid; o < a.n_dir; o += NT) {
-                const int it = o % a.n_theta, ip = o / a.n_theta;
-                float2 acc = make_float2(0.f, 0.f);
-                for (int aa = 0; aa < d.rt; ++aa) cfma(acc, s_ut[it + a.L.ldt * aa], s_V[ip + a.L.ldv * aa]);
-                out[o] = acc;
+            {
+                float2* out = a.spec + (((int64_t)r * a.G + d.g) * 2 + d.alpha) * a.n_dir;
+                const int ldt = a.L.ldt, ldv = a.L.ldv, nth = a.n_theta;
+                smem_gemm<2, 4>(nth, a.n_phi, d.rt, [&](int it, int aa) { return s_ut[it + ldt * aa]; },
+                                [&](int aa, int ip) { return s_V[ip + ldv * aa]; },
+                                [&](int it, int ip, float2 v) { out[it + nth * ip] = v; });
             }
             __syncthreads();
         }
@@ -333,20 +374,16 @@ __global__ void __launch_bounds__(512, 3) tucker_disaggregate_kernel(const DisAr
                 }
                 __syncthreads();
                 // DG1: P = U_theta^T conj(W g), then H = P U_phi
-                for (int o = tid; o < d.rt * a.n_phi; o += NT) {
-                    const int aa = o % d.rt, ip = o / d.rt;
-                    float2 acc = make_float2(0.f, 0.f);
-                    for (int it = 0; it < a.n_theta; ++it) cfma(acc, s_ut[it + a.L.ldt * aa], s_G[it + a.L.ldg * ip]);
-                    s_P[aa + d.rt * ip] = acc;
-                }
-                __syncthreads();
-                for (int o = tid; o < d.ld_ab; o += NT) {
-                    float2 acc = make_float2(0.f, 0.f);
-                    if (o < d.rt * d.rp) {
-                        const int aa = o % d.rt, b = o / d.rt;
-                        for (int ip = 0; ip < a.n_phi; ++ip) cfma(acc, s_P[aa + d.rt * ip], s_up[ip + a.L.ldp * b]);
-                    }
-                    s_H[o] = acc;
+                {
+                    const int ldt = a.L.ldt, ldg = a.L.ldg, ldp = a.L.ldp, rt = d.rt;
+                    smem_gemm<2, 4>(rt, a.n_phi, a.n_theta, [&](int aa, int it) { return s_ut[it + ldt * aa]; },
+                                    [&](int it, int ip) { return s_G[it + ldg * ip]; },
+                                    [&](int aa, int ip, float2 v) { s_P[aa + rt * ip] = v; });
+                    __syncthreads();
+                    smem_gemm<2, 2>(rt, d.rp, a.n_phi, [&](int aa, int ip) { return s_P[aa + rt * ip]; },
+                                    [&](int ip, int b) { return s_up[ip + ldp * b]; },
+                                    [&](int aa, int b, float2 v) { s_H[aa + rt * b] = v; });
+                    for (int o = rt * d.rp + tid; o < d.ld_ab; o += NT) s_H[o] = make_float2(0.f, 0.f);
                 }
                 __syncthreads();
                 }
@@ -563,6 +600,219 @@ SmemLayout dis_layout(const Plan& P, int NT) {
     return L;
 }
 
+// ------------------------------------------------------------------ split path
+// Plans with few, large work items (the trihedral's 19 groups: 38 items for 152 SMs)
+// leave most SMs idle with one item per CTA.  The split path runs each stage as three
+// launches that spread every item over many CTAs, with the items' intermediates in
+// plan-owned scratch (t / s: r_beta, M / H: ld_ab complex per item):
+//   aggregation     SA1: t = U_beta^T x_g, blocks of kSplitRows rows per CTA (Fig. 2b step 1)
+//                   SA2: M = C_(3)^T t, blocks of kSplitCols column pairs per CTA
+//                   SA3: AG3 + AG4 from M, one CTA per item (Fig. 2b steps 2-4)
+//   disaggregation  SD1: H = U_theta^T conj(W g) U_phi, one CTA per item (Fig. 3b step 1)
+//                   SD2: s = C_(3) vec(H), blocks of rows (step 2)
+//                   SD3: y_g = beta y_g + conj(sum_alpha U_beta s), blocks of column pairs of
+//                        U_beta^T covering both components of a group (step 3)
+constexpr int kSplitRows = 16;  // one row per warp of 512 threads
+constexpr int kSplitCols = 64;  // float4 (two complex) columns per CTA: 8 slices of rows
+
+struct SplitTile { int item, start; };  // item (or group for SD3) and first row / column pair
+
+struct SplitArgs {
+    const TuckerItem* items;
+    const SplitTile* tiles;
+    const float2* fac;
+    const int* grp_rwg;
+    const float2* x;      // SA1
+    int64_t ldx;
+    const float2* spec;   // SD1 input
+    const float* w;       // SD1 weights or null
+    float2* spec_out;     // SA3 output
+    float2* y;            // SD3 output
+    int64_t ldy;
+    float2 beta;
+    float2* scratch;      // per item: [r_beta slot | ld_ab slot] (offsets in TuckerItem order)
+    const int64_t* scr_off;
+    int n_theta, n_phi, n_dir, G, r;
+    SmemLayout L;
+};
+
+// out[j0 + j] = sum_{c < nrows} M[c][j0 + j] s[c] for j < cbv (float4 columns): the CTA
+// splits into NT / kSplitCols slices of rows, summed through `part` (NT float4).
+template <class Emit>
+__device__ __forceinline__ void colblock_axpy(const float4* __restrict__ M, int64_t ld2, int j0, int cbv, int nrows,
+                                              const float2* s, float4* part, Emit emit) {
+    const int tid = threadIdx.x, S = blockDim.x / kSplitCols;
+    const int j = tid % kSplitCols, sl = tid / kSplitCols;
+    float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+    if (j < cbv && sl < S) {
+        const float4* col = M + j0 + j;
+        int c = sl;
+#pragma unroll 2
+        for (; c + S < nrows; c += 2 * S) {
+            const float4 m0 = ld_stream(col + (int64_t)c * ld2);
+            const float4 m1 = ld_stream(col + (int64_t)(c + S) * ld2);
+            cfma2(a0, m0, s[c]);
+            cfma2(a1, m1, s[c + S]);
+        }
+        if (c < nrows) cfma2(a0, ld_stream(col + (int64_t)c * ld2), s[c]);
+    }
+    if (sl < S) part[sl * kSplitCols + j] = add4(a0, a1);
+    __syncthreads();
+    for (int jj = tid; jj < cbv; jj += blockDim.x) {
+        float4 a = part[jj];
+        for (int q = 1; q < S; ++q) a = add4(a, part[q * kSplitCols + jj]);
+        emit(j0 + jj, a);
+    }
+}
+
+// SA1: t[c] = sum_n U_beta[n, c] x_n for the rows c of one tile
+__global__ void __launch_bounds__(512) split_ag1_kernel(const SplitArgs a) {
+    extern __shared__ float4 smem4[];
+    float2* s_x = reinterpret_cast<float2*>(smem4);
+    const SplitTile t = a.tiles[blockIdx.x];
+    const TuckerItem d = a.items[t.item];
+    for (int n = threadIdx.x; n < d.ld_nb; n += blockDim.x)
+        s_x[n] = n < d.n_beta ? a.x[(int64_t)a.grp_rwg[d.rwg + n] + a.ldx * a.r] : make_float2(0.f, 0.f);
+    __syncthreads();
+    float2* tout = a.scratch + a.scr_off[t.item];
+    const int rows = min(kSplitRows, d.rb - t.start);
+    rowdot<false>(reinterpret_cast<const float4*>(a.fac + d.ub) + (int64_t)t.start * (d.ld_nb / 2), d.ld_nb / 2, rows,
+                  reinterpret_cast<const float4*>(s_x), [&](int c, float2 v) { tout[t.start + c] = v; });
+}
+
+// SA2: M[ab] = sum_c C_(3)[c, ab] t[c] for the column pairs of one tile
+__global__ void __launch_bounds__(512) split_ag2_kernel(const SplitArgs a) {
+    extern __shared__ float4 smem4[];
+    float4* s_part = smem4;
+    float2* s_t = reinterpret_cast<float2*>(smem4 + blockDim.x);
+    const SplitTile t = a.tiles[blockIdx.x];
+    const TuckerItem d = a.items[t.item];
+    const float2* tin = a.scratch + a.scr_off[t.item];
+    for (int c = threadIdx.x; c < d.rb; c += blockDim.x) s_t[c] = tin[c];
+    __syncthreads();
+    float4* mout = reinterpret_cast<float4*>(a.scratch + a.scr_off[t.item] + round_up_dev(d.rb, 2));
+    const int ld2 = d.ld_ab / 2;
+    colblock_axpy(reinterpret_cast<const float4*>(a.fac + d.core), ld2, t.start, min(kSplitCols, ld2 - t.start), d.rb,
+                  s_t, s_part, [&](int j, float4 v) { mout[j] = v; });
+}
+
+// SA3: AG3 + AG4 of one item from its M (one CTA per item)
+__global__ void __launch_bounds__(512) split_ag34_kernel(const SplitArgs a) {
+    extern __shared__ float4 smem4[];
+    float2* sm = reinterpret_cast<float2*>(smem4);
+    float2* s_ut = sm + a.L.o_a;
+    float2* s_up = sm + a.L.o_b;
+    float2* s_V = sm + a.L.o_c;
+    float2* s_M = sm + a.L.o_e;
+    const int q = blockIdx.x, NT = blockDim.x, tid = threadIdx.x;
+    const TuckerItem d = a.items[q];
+    const float2* Ut = a.fac + d.uth;
+    const float2* Up = a.fac + d.uphi;
+    const float2* min_ = a.scratch + a.scr_off[q] + round_up_dev(d.rb, 2);
+    for (int e = tid; e < a.n_theta * d.rt; e += NT) s_ut[(e % a.n_theta) + a.L.ldt * (e / a.n_theta)] = Ut[e];
+    for (int e = tid; e < a.n_phi * d.rp; e += NT) s_up[(e % a.n_phi) + a.L.ldp * (e / a.n_phi)] = Up[e];
+    for (int e = tid; e < d.rt * d.rp; e += NT) s_M[e] = min_[e];
+    __syncthreads();
+    {
+        const int ldp = a.L.ldp, ldv = a.L.ldv, rt = d.rt;
+        smem_gemm<2, 2>(a.n_phi, rt, d.rp, [&](int ip, int b) { return s_up[ip + ldp * b]; },
+                        [&](int b, int aa) { return s_M[aa + rt * b]; },
+                        [&](int ip, int aa, float2 v) { s_V[ip + ldv * aa] = v; });
+    }
+    __syncthreads();
+    float2* out = a.spec_out + (((int64_t)a.r * a.G + d.g) * 2 + d.alpha) * a.n_dir;
+    const int ldt = a.L.ldt, ldv = a.L.ldv, nth = a.n_theta;
+    smem_gemm<2, 4>(nth, a.n_phi, d.rt, [&](int it, int aa) { return s_ut[it + ldt * aa]; },
+                    [&](int aa, int ip) { return s_V[ip + ldv * aa]; },
+                    [&](int it, int ip, float2 v) { out[it + nth * ip] = v; });
+}
+
+// SD1: H = U_theta^T conj(W g) U_phi of one item (one CTA per item), zero-padded to ld_ab
+__global__ void __launch_bounds__(512) split_dg1_kernel(const SplitArgs a) {
+    extern __shared__ float4 smem4[];
+    float2* sm = reinterpret_cast<float2*>(smem4);
+    float2* s_ut = sm + a.L.o_a;
+    float2* s_up = sm + a.L.o_b;
+    float2* s_G = sm + a.L.o_f;
+    float2* s_P = sm + a.L.o_g;
+    const int q = blockIdx.x, NT = blockDim.x, tid = threadIdx.x;
+    const TuckerItem d = a.items[q];
+    const float2* Ut = a.fac + d.uth;
+    const float2* Up = a.fac + d.uphi;
+    const float2* gin = a.spec + (((int64_t)a.r * a.G + d.g) * 2 + d.alpha) * a.n_dir;
+    for (int e = tid; e < a.n_theta * d.rt; e += NT) s_ut[(e % a.n_theta) + a.L.ldt * (e / a.n_theta)] = Ut[e];
+    for (int e = tid; e < a.n_phi * d.rp; e += NT) s_up[(e % a.n_phi) + a.L.ldp * (e / a.n_phi)] = Up[e];
+    for (int o = tid; o < a.n_dir; o += NT) {
+        const float2 v = gin[o];
+        const float wt = a.w ? a.w[o] : 1.0f;
+        s_G[(o % a.n_theta) + a.L.ldg * (o / a.n_theta)] = make_float2(wt * v.x, -wt * v.y);
+    }
+    __syncthreads();
+    const int ldt = a.L.ldt, ldg = a.L.ldg, ldp = a.L.ldp, rt = d.rt;
+    smem_gemm<2, 4>(rt, a.n_phi, a.n_theta, [&](int aa, int it) { return s_ut[it + ldt * aa]; },
+                    [&](int it, int ip) { return s_G[it + ldg * ip]; },
+                    [&](int aa, int ip, float2 v) { s_P[aa + rt * ip] = v; });
+    __syncthreads();
+    float2* hout = a.scratch + a.scr_off[q] + round_up_dev(d.rb, 2);
+    smem_gemm<2, 2>(rt, d.rp, a.n_phi, [&](int aa, int ip) { return s_P[aa + rt * ip]; },
+                    [&](int ip, int b) { return s_up[ip + ldp * b]; },
+                    [&](int aa, int b, float2 v) { hout[aa + rt * b] = v; });
+    for (int o = rt * d.rp + tid; o < d.ld_ab; o += NT) hout[o] = make_float2(0.f, 0.f);
+}
+
+// SD2: s[c] = sum_ab C_(3)[c, ab] H[ab] for the rows c of one tile
+__global__ void __launch_bounds__(512) split_dg2_kernel(const SplitArgs a) {
+    extern __shared__ float4 smem4[];
+    float2* s_H = reinterpret_cast<float2*>(smem4);
+    const SplitTile t = a.tiles[blockIdx.x];
+    const TuckerItem d = a.items[t.item];
+    float2* slot = a.scratch + a.scr_off[t.item];
+    const float2* hin = slot + round_up_dev(d.rb, 2);
+    for (int o = threadIdx.x; o < d.ld_ab; o += blockDim.x) s_H[o] = hin[o];
+    __syncthreads();
+    const int rows = min(kSplitRows, d.rb - t.start);
+    rowdot<false>(reinterpret_cast<const float4*>(a.fac + d.core) + (int64_t)t.start * (d.ld_ab / 2), d.ld_ab / 2, rows,
+                  reinterpret_cast<const float4*>(s_H), [&](int c, float2 v) { slot[t.start + c] = v; });
+}
+
+// SD3: y = beta y + conj(U_beta^(0) s^(0) + U_beta^(1) s^(1)) for the column pairs of one
+// tile of group t.item (both components)
+__global__ void __launch_bounds__(512) split_dg3_kernel(const SplitArgs a) {
+    extern __shared__ float4 smem4[];
+    float4* s_part = smem4;
+    float4* s_acc = smem4 + blockDim.x;
+    float2* s_s = reinterpret_cast<float2*>(smem4 + blockDim.x + kSplitCols);
+    const SplitTile t = a.tiles[blockIdx.x];
+    const int g = t.item;
+    const TuckerItem d0 = a.items[2 * g];
+    const int ld2 = d0.ld_nb / 2, cbv = min(kSplitCols, ld2 - t.start);
+    for (int al = 0; al < 2; ++al) {
+        const TuckerItem d = a.items[2 * g + al];
+        const float2* sin_ = a.scratch + a.scr_off[2 * g + al];
+        for (int c = threadIdx.x; c < d.rb; c += blockDim.x) s_s[c] = sin_[c];
+        __syncthreads();
+        colblock_axpy(reinterpret_cast<const float4*>(a.fac + d.ub), ld2, t.start, cbv, d.rb, s_s, s_part,
+                      [&](int j, float4 v) {
+                          const int jj = j - t.start;
+                          s_acc[jj] = al == 0 ? v : add4(s_acc[jj], v);
+                      });
+        __syncthreads();
+    }
+    for (int jj = threadIdx.x; jj < 2 * cbv; jj += blockDim.x) {
+        const int n = 2 * t.start + jj;
+        if (n >= d0.n_beta) continue;
+        const float4 v4 = s_acc[jj >> 1];
+        float2 v = (jj & 1) ? make_float2(v4.z, -v4.w) : make_float2(v4.x, -v4.y);
+        float2* dst = a.y + (int64_t)a.grp_rwg[d0.rwg + n] + a.ldy * a.r;
+        if (a.beta.x != 0.f || a.beta.y != 0.f) {
+            const float2 old = *dst;
+            v.x += a.beta.x * old.x - a.beta.y * old.y;
+            v.y += a.beta.x * old.y + a.beta.y * old.x;
+        }
+        *dst = v;
+    }
+}
+
 template <class K>
 Schedule make_schedule(K kernel, int NT, size_t smem, int num_sms, int n_items, int ctas_per_sm = 0) {
     Schedule s;
@@ -632,7 +882,7 @@ void pack_factors_fp32(Plan& P, cudaStream_t s) {
     P.factor_elems_alg = alg;
     if (P.d_factors) cudaFree(P.d_factors);
     P.d_factors = nullptr;
-    TFMM_CUDA_CHECK(cudaMalloc(&P.d_factors, sizeof(float2) * std::max<int64_t>(off, 1)));
+    TFMM_CUDA_CHECK(device_malloc(&P.d_factors, sizeof(float2) * std::max<int64_t>(off, 1)));
     TFMM_CUDA_CHECK(cudaMemsetAsync(P.d_factors, 0, sizeof(float2) * std::max<int64_t>(off, 1), s));
     for (int g = 0; g < P.G; ++g)
         for (int al = 0; al < 2; ++al) {
@@ -657,10 +907,12 @@ void finalize_hot_layout(Plan& P, cudaStream_t s) {
     const int nI = P.G * 2;
     if (P.d_items) cudaFree(P.d_items);
     P.d_items = nullptr;
-    TFMM_CUDA_CHECK(cudaMalloc(&P.d_items, sizeof(TuckerItem) * nI));
+    TFMM_CUDA_CHECK(device_malloc(&P.d_items, sizeof(TuckerItem) * nI));
     TFMM_CUDA_CHECK(cudaMemcpyAsync(P.d_items, P.items.data(), sizeof(TuckerItem) * nI, cudaMemcpyHostToDevice, s));
     configure_hot(P, P.tuning, s);
 }
+
+void configure_split(Plan& P, cudaStream_t s);
 
 // Queue orders (0: most factor bytes first, the LPT rule; 1: group order) and
 // persistent grids (threads per CTA, CTAs per SM capped by occupancy) of the
@@ -671,6 +923,7 @@ void configure_hot(Plan& P, const HotTuning& t, cudaStream_t s) {
     TFMM_REQUIRE(ok_threads(t.agg_threads) && ok_threads(t.dis_threads), "threads per CTA must be 64..512, a multiple of 32");
     TFMM_REQUIRE(t.agg_ctas_per_sm >= 0 && t.dis_ctas_per_sm >= 0, "CTAs per SM must be >= 0");
     TFMM_REQUIRE((t.agg_order == 0 || t.agg_order == 1) && (t.dis_order == 0 || t.dis_order == 1), "order must be 0 or 1");
+    TFMM_REQUIRE(t.split >= 0 && t.split <= 2, "split must be 0 (automatic), 1 (always) or 2 (never)");
     auto bytes = [&](const TuckerItem& d) {
         return (double)d.rb * d.ld_nb + (double)d.rb * d.ld_ab + (double)P.n_phi * d.rp + (double)P.n_theta * d.rt;
     };
@@ -683,8 +936,8 @@ void configure_hot(Plan& P, const HotTuning& t, cudaStream_t s) {
         std::stable_sort(dis.begin(), dis.end(), [&](int a, int b) {
             return bytes(P.items[2 * a]) + bytes(P.items[2 * a + 1]) > bytes(P.items[2 * b]) + bytes(P.items[2 * b + 1]);
         });
-    if (!P.d_agg_order) TFMM_CUDA_CHECK(cudaMalloc(&P.d_agg_order, sizeof(int) * nI));
-    if (!P.d_dis_order) TFMM_CUDA_CHECK(cudaMalloc(&P.d_dis_order, sizeof(int) * std::max(P.G, 1)));
+    if (!P.d_agg_order) TFMM_CUDA_CHECK(device_malloc(&P.d_agg_order, sizeof(int) * nI));
+    if (!P.d_dis_order) TFMM_CUDA_CHECK(device_malloc(&P.d_dis_order, sizeof(int) * std::max(P.G, 1)));
     // stream-ordered: launches already queued keep reading the old order until these copies land
     TFMM_CUDA_CHECK(cudaMemcpyAsync(P.d_agg_order, agg.data(), sizeof(int) * nI, cudaMemcpyHostToDevice, s));
     TFMM_CUDA_CHECK(cudaMemcpyAsync(P.d_dis_order, dis.data(), sizeof(int) * P.G, cudaMemcpyHostToDevice, s));
@@ -705,7 +958,62 @@ void configure_hot(Plan& P, const HotTuning& t, cudaStream_t s) {
     }
     P.tuning = t;
     P.hot_ok = P.agg_sched.blocks > 0 && P.dis_sched.blocks > 0;
+    const bool want_split = !plan_is_svd(P) && P.hot_ok && (t.split == 1 || (t.split == 0 && nI < 2 * P.num_sms));
+    if (want_split != (bool)P.split) {  // captured graphs point into the split path's scratch
+        TFMM_REQUIRE(P.live_graphs == 0, "destroy the plan's graphs before changing the single-RHS path");
+        P.split.reset();
+        if (want_split) configure_split(P, s);
+    }
     TFMM_CUDA_CHECK(cudaStreamSynchronize(s));
+}
+
+// Tile lists, scratch and shared-memory sizes of the split path.
+void configure_split(Plan& P, cudaStream_t s) {
+    auto SP = std::make_unique<SplitPlan>();
+    const int nI = P.G * 2, NT = 512;
+    std::vector<SplitTile> a1, a2, d2, d3;
+    std::vector<int64_t> off(nI);
+    int64_t tot = 0;
+    for (int q = 0; q < nI; ++q) {
+        const TuckerItem& d = P.items[q];
+        off[q] = tot;
+        tot += round_up(d.rb, 2) + d.ld_ab;
+        for (int c = 0; c < d.rb; c += kSplitRows) {
+            a1.push_back(SplitTile{q, c});
+            d2.push_back(SplitTile{q, c});
+        }
+        for (int j = 0; j < d.ld_ab / 2; j += kSplitCols) a2.push_back(SplitTile{q, j});
+    }
+    for (int g = 0; g < P.G; ++g)
+        for (int j = 0; j < P.items[2 * g].ld_nb / 2; j += kSplitCols) d3.push_back(SplitTile{g, j});
+    auto up = [&](DeviceBuffer& b, const std::vector<SplitTile>& v, int& n) {
+        n = (int)v.size();
+        TFMM_CUDA_CHECK(device_malloc(&b.p, sizeof(SplitTile) * std::max<size_t>(v.size(), 1)));
+        TFMM_CUDA_CHECK(cudaMemcpyAsync(b.p, v.data(), sizeof(SplitTile) * v.size(), cudaMemcpyHostToDevice, s));
+    };
+    up(SP->t_ag1, a1, SP->n_ag1);
+    up(SP->t_ag2, a2, SP->n_ag2);
+    up(SP->t_dg2, d2, SP->n_dg2);
+    up(SP->t_dg3, d3, SP->n_dg3);
+    TFMM_CUDA_CHECK(device_malloc(&SP->scratch.p, sizeof(float2) * std::max<int64_t>(tot, 1)));
+    TFMM_CUDA_CHECK(device_malloc(&SP->scr_off.p, sizeof(int64_t) * nI));
+    TFMM_CUDA_CHECK(cudaMemcpyAsync(SP->scr_off.p, off.data(), sizeof(int64_t) * nI, cudaMemcpyHostToDevice, s));
+    SP->smem_ag1 = sizeof(float2) * al16(P.max_ldnb);
+    SP->smem_ag2 = sizeof(float4) * NT + sizeof(float2) * al16(P.max_rank[2]);
+    SP->smem_ag34 = sizeof(float2) * agg_layout(P, NT).total;
+    SP->smem_dg1 = sizeof(float2) * dis_layout(P, NT).total;
+    SP->smem_dg2 = sizeof(float2) * al16(P.max_ldab);
+    SP->smem_dg3 = sizeof(float4) * (NT + kSplitCols) + sizeof(float2) * al16(P.max_rank[2]);
+    auto allow = [](const void* k, size_t bytes) {
+        if (bytes > 48 * 1024) TFMM_CUDA_CHECK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    };
+    allow((const void*)split_ag1_kernel, SP->smem_ag1);
+    allow((const void*)split_ag2_kernel, SP->smem_ag2);
+    allow((const void*)split_ag34_kernel, SP->smem_ag34);
+    allow((const void*)split_dg1_kernel, SP->smem_dg1);
+    allow((const void*)split_dg2_kernel, SP->smem_dg2);
+    allow((const void*)split_dg3_kernel, SP->smem_dg3);
+    P.split = std::move(SP);
 }
 
 void finalize_dense_layout(Plan& P) {
@@ -725,10 +1033,10 @@ void finalize_dense_layout(Plan& P) {
     std::iota(dis.begin(), dis.end(), 0);
     std::stable_sort(agg.begin(), agg.end(), [&](int a, int b) { return items[a].n_beta > items[b].n_beta; });
     std::stable_sort(dis.begin(), dis.end(), [&](int a, int b) { return items[2 * a].n_beta > items[2 * b].n_beta; });
-    TFMM_CUDA_CHECK(cudaMalloc(&P.d_dense_items, sizeof(DenseItem) * nI));
+    TFMM_CUDA_CHECK(device_malloc(&P.d_dense_items, sizeof(DenseItem) * nI));
     TFMM_CUDA_CHECK(cudaMemcpy(P.d_dense_items, items.data(), sizeof(DenseItem) * nI, cudaMemcpyHostToDevice));
-    TFMM_CUDA_CHECK(cudaMalloc(&P.d_dense_agg_order, sizeof(int) * nI));
-    TFMM_CUDA_CHECK(cudaMalloc(&P.d_dense_dis_order, sizeof(int) * std::max(P.G, 1)));
+    TFMM_CUDA_CHECK(device_malloc(&P.d_dense_agg_order, sizeof(int) * nI));
+    TFMM_CUDA_CHECK(device_malloc(&P.d_dense_dis_order, sizeof(int) * std::max(P.G, 1)));
     TFMM_CUDA_CHECK(cudaMemcpy(P.d_dense_agg_order, agg.data(), sizeof(int) * nI, cudaMemcpyHostToDevice));
     TFMM_CUDA_CHECK(cudaMemcpy(P.d_dense_dis_order, dis.data(), sizeof(int) * P.G, cudaMemcpyHostToDevice));
     const int NT = 512;
@@ -746,8 +1054,68 @@ void pack_dense_fp32_from_f64(Plan& P, const double2* src, int g, int alpha, cud
     TFMM_CUDA_CHECK(cudaGetLastError());
 }
 
+namespace {
+
+SplitArgs split_args(const Plan& P, int r) {
+    SplitArgs a{};
+    a.items = P.d_items;
+    a.fac = P.d_factors;
+    a.grp_rwg = P.d_grp_rwg;
+    a.scratch = static_cast<float2*>(P.split->scratch.p);
+    a.scr_off = static_cast<const int64_t*>(P.split->scr_off.p);
+    a.n_theta = P.n_theta;
+    a.n_phi = P.n_phi;
+    a.n_dir = P.n_dir;
+    a.G = P.G;
+    a.r = r;
+    return a;
+}
+
+void launch_split_aggregate(const Plan& P, const float2* x, int R, int64_t ldx, float2* spec, cudaStream_t s) {
+    const SplitPlan& S = *P.split;
+    for (int r = 0; r < R; ++r) {
+        SplitArgs a = split_args(P, r);
+        a.x = x;
+        a.ldx = ldx;
+        a.spec_out = spec;
+        a.tiles = static_cast<const SplitTile*>(S.t_ag1.p);
+        split_ag1_kernel<<<S.n_ag1, 512, S.smem_ag1, s>>>(a);
+        a.tiles = static_cast<const SplitTile*>(S.t_ag2.p);
+        split_ag2_kernel<<<S.n_ag2, 512, S.smem_ag2, s>>>(a);
+        a.L = agg_layout(P, 512);
+        split_ag34_kernel<<<P.G * 2, 512, S.smem_ag34, s>>>(a);
+        TFMM_CUDA_CHECK(cudaGetLastError());
+    }
+}
+
+void launch_split_disaggregate(const Plan& P, const float2* spec, int R, int weights, float2 beta, float2* y,
+                               int64_t ldy, cudaStream_t s) {
+    const SplitPlan& S = *P.split;
+    for (int r = 0; r < R; ++r) {
+        SplitArgs a = split_args(P, r);
+        a.spec = spec;
+        a.w = weights ? P.d_weights : nullptr;
+        a.y = y;
+        a.ldy = ldy;
+        a.beta = beta;
+        a.L = dis_layout(P, 512);
+        split_dg1_kernel<<<P.G * 2, 512, S.smem_dg1, s>>>(a);
+        a.tiles = static_cast<const SplitTile*>(S.t_dg2.p);
+        split_dg2_kernel<<<S.n_dg2, 512, S.smem_dg2, s>>>(a);
+        a.tiles = static_cast<const SplitTile*>(S.t_dg3.p);
+        split_dg3_kernel<<<S.n_dg3, 512, S.smem_dg3, s>>>(a);
+        TFMM_CUDA_CHECK(cudaGetLastError());
+    }
+}
+
+}  // namespace
+
 void launch_tucker_aggregate(const Plan& P, const float2* x, int R, int64_t ldx, float2* spec, cudaStream_t s) {
     TFMM_REQUIRE(P.hot_ok, "single-RHS kernels unavailable for this plan (work item exceeds one CTA)");
+    if (P.split) {
+        launch_split_aggregate(P, x, R, ldx, spec, s);
+        return;
+    }
     AggArgs a;
     a.items = P.d_items;
     a.order = P.d_agg_order;
@@ -777,6 +1145,10 @@ void launch_tucker_aggregate(const Plan& P, const float2* x, int R, int64_t ldx,
 void launch_tucker_disaggregate(const Plan& P, const float2* spec, int R, int weights, float2 beta, float2* y,
                                 int64_t ldy, cudaStream_t s) {
     TFMM_REQUIRE(P.hot_ok, "single-RHS kernels unavailable for this plan (work item exceeds one CTA)");
+    if (P.split) {
+        launch_split_disaggregate(P, spec, R, weights, beta, y, ldy, s);
+        return;
+    }
     DisArgs a;
     a.items = P.d_items;
     a.order = P.d_dis_order;

@@ -31,6 +31,14 @@ struct Error : std::runtime_error {
         }                                                                                           \
     } while (0)
 
+// Every device allocation of the library goes through device_malloc, so that the
+// test hook tfmm_test_fail_allocation can make the n-th one fail (TFMM_OOM).
+cudaError_t device_malloc_bytes(void** p, size_t bytes);
+template <class T>
+inline cudaError_t device_malloc(T** p, size_t bytes) {
+    return device_malloc_bytes(reinterpret_cast<void**>(p), bytes);
+}
+
 #define TFMM_REQUIRE(cond, msg)                                                                     \
     do {                                                                                            \
         if (!(cond)) ::tfmm::fail(TFMM_INVALID_ARG, msg);                                           \
@@ -165,10 +173,34 @@ struct TcPlan {             // per (R, terms): problem lists of the 8 steps and 
     ~TcPlan();
 };
 
+// Translation stage (FMM-FFT): zero-padded box grid, transform of the translation
+// kernel and the cuFFT plan of the hot path (built on first use).
+struct TransPlan {
+    int N[3] = {1, 1, 1};    // FFT grid N_x, N_y, N_z >= 2K - 1
+    int64_t Ns = 0;          // grid points
+    int nb = 0;              // interleaved transforms per right-hand side: 2 N_dir
+    int fft = 0;             // cufftHandle (C2C, nb transforms)
+    DeviceBuffer That;       // N_dir x Ns FP32 complex: transform of (-jk/16 pi^2) T_L over the grid
+    DeviceBuffer grid;       // nb x Ns FP32 complex work array (one transform after the other)
+    DeviceBuffer group_cell; // G int: grid point of each group
+    ~TransPlan();
+};
+
 // Launch shape and queue order of the single-RHS kernels (set by the autotuner).
 struct HotTuning {
     int agg_threads = 512, agg_ctas_per_sm = 0, agg_order = 0;  // ctas 0: as many as fit
     int dis_threads = 512, dis_ctas_per_sm = 0, dis_order = 0;  // order 0: longest first, 1: group order
+    int split = 0;  // split path: 0 automatic (fewer work items than 2 x SMs), 1 always, 2 never
+};
+
+// Split path of the single-RHS stages (plans with few, large items): tile lists of the
+// row- and column-block launches and the items' intermediates.
+struct SplitPlan {
+    DeviceBuffer t_ag1, t_ag2, t_dg2, t_dg3;  // SplitTile lists
+    int n_ag1 = 0, n_ag2 = 0, n_dg2 = 0, n_dg3 = 0;
+    DeviceBuffer scratch;                     // per item: r_beta (padded to 2) + ld_ab complex
+    DeviceBuffer scr_off;                     // per item: offset of its slot (complex elements)
+    size_t smem_ag1 = 0, smem_ag2 = 0, smem_ag34 = 0, smem_dg1 = 0, smem_dg2 = 0, smem_dg3 = 0;
 };
 
 struct Schedule {
@@ -219,6 +251,7 @@ struct Plan {
     int tc_f34_n1 = 0;                 // cap on r_theta x RHS per CTA of the fused AG3+AG4 kernel (0: largest that fits)
     int tc_dg1a_pairs = 0;             // (i_phi, r) pairs per CTA of the DG1a kernel (0: 128 when it fits, else 64)
     bool hot_ok = false;               // the single-RHS kernels fit (shared memory of the largest item)
+    std::unique_ptr<SplitPlan> split;  // set when the single-RHS stages run the split path
     double tuned_ms[2] = {0, 0};       // autotuner's best aggregate / disaggregate times
     int live_graphs = 0;               // captured graphs that still point into this plan
     int max_nb = 0, max_ldnb = 0, max_rank[3] = {0, 0, 0}, max_ldab = 0;
@@ -242,6 +275,8 @@ struct Plan {
     std::vector<TcItem> tc_items[4];
     DeviceBuffer tc_err;               // int: waits that gave up
     std::vector<std::unique_ptr<TcPlan>> tc;
+    // translation stage (built on the first tfmm_translate)
+    std::unique_ptr<TransPlan> trans;
     // workspace of tfmm_matvec_host
     int ws_R = 0;
     float2 *d_ws_x = nullptr, *d_ws_spec = nullptr, *d_ws_y = nullptr;
@@ -296,6 +331,9 @@ void tc_replan_shapes(Plan& P);  // re-plans the fused AG3+AG4 and DG1a kernels 
 void launch_tc_aggregate(Plan& P, int T, const float2* x, int R, int64_t ldx, float2* spec, cudaStream_t s);
 void launch_tc_disaggregate(Plan& P, int T, const float2* spec, int R, int weights, float2 beta, float2* y,
                             int64_t ldy, cudaStream_t s);
+// translate.cu
+void build_translation(Plan& P, cudaStream_t s);
+void launch_translate(Plan& P, const float2* spec_out, int R, float2* spec_in, cudaStream_t s);
 // mrhs.cu
 MrPlan* get_mr_plan(Plan& P, int R);
 void launch_mr_aggregate(Plan& P, const float2* x, int R, int64_t ldx, float2* spec, cudaStream_t s);

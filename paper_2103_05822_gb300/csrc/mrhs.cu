@@ -189,8 +189,8 @@ void launch_stage(const Plan& P, const MrStage& st, Ctx c, cudaStream_t s) {
 
 void upload_stage(MrStage& st, const std::vector<MrProb>& probs, const std::vector<MrTile>& tiles) {
     st.n_tiles = (int)tiles.size();
-    TFMM_CUDA_CHECK(cudaMalloc(&st.d_probs, sizeof(MrProb) * std::max<size_t>(probs.size(), 1)));
-    TFMM_CUDA_CHECK(cudaMalloc(&st.d_tiles, sizeof(MrTile) * std::max<size_t>(tiles.size(), 1)));
+    TFMM_CUDA_CHECK(device_malloc(&st.d_probs, sizeof(MrProb) * std::max<size_t>(probs.size(), 1)));
+    TFMM_CUDA_CHECK(device_malloc(&st.d_tiles, sizeof(MrTile) * std::max<size_t>(tiles.size(), 1)));
     TFMM_CUDA_CHECK(cudaMemcpy(st.d_probs, probs.data(), sizeof(MrProb) * probs.size(), cudaMemcpyHostToDevice));
     TFMM_CUDA_CHECK(cudaMemcpy(st.d_tiles, tiles.data(), sizeof(MrTile) * tiles.size(), cudaMemcpyHostToDevice));
 }
@@ -228,9 +228,9 @@ MrPlan* get_mr_plan(Plan& P, int R) {
         o3[q] = off3;
         off3 += (int64_t)std::max(np, nt) * d.rt * R;
     }
-    TFMM_CUDA_CHECK(cudaMalloc(&M.buf[0], sizeof(float2) * std::max<int64_t>(off1, 1)));
-    TFMM_CUDA_CHECK(cudaMalloc(&M.buf[1], sizeof(float2) * std::max<int64_t>(off2, 1)));
-    TFMM_CUDA_CHECK(cudaMalloc(&M.buf[2], sizeof(float2) * std::max<int64_t>(off3, 1)));
+    TFMM_CUDA_CHECK(device_malloc(&M.buf[0], sizeof(float2) * std::max<int64_t>(off1, 1)));
+    TFMM_CUDA_CHECK(device_malloc(&M.buf[1], sizeof(float2) * std::max<int64_t>(off2, 1)));
+    TFMM_CUDA_CHECK(device_malloc(&M.buf[2], sizeof(float2) * std::max<int64_t>(off3, 1)));
     std::vector<MrProb> pr[8];
     std::vector<MrTile> tl[8];
     for (int q = 0; q < P.G * 2; ++q) {

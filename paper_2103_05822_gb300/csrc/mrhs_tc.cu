@@ -1105,7 +1105,7 @@ void build_tc_factors(Plan& P, int T, cudaStream_t s) {
         add(t.uthT, nt, d.rt);        // [i_theta][a]
         add(t.uth, d.rt, nt);         // [a][i_theta]
     }
-    TFMM_CUDA_CHECK(cudaMalloc(&P.tc_fac[T].p, sizeof(bf16) * std::max<int64_t>(off, 1)));
+    TFMM_CUDA_CHECK(device_malloc(&P.tc_fac[T].p, sizeof(bf16) * std::max<int64_t>(off, 1)));
     TFMM_CUDA_CHECK(cudaMemsetAsync(P.tc_fac[T].p, 0, sizeof(bf16) * std::max<int64_t>(off, 1), s));
     bf16* base = reinterpret_cast<bf16*>(P.tc_fac[T].p);
     auto conv = [&](const float2* src, int rows, int cols, int64_t sr, int64_t sk, const TcMat& m) {
@@ -1135,7 +1135,7 @@ void build_tc_factors(Plan& P, int T, cudaStream_t s) {
     TFMM_CUDA_CHECK(cudaGetLastError());
     TFMM_CUDA_CHECK(cudaStreamSynchronize(s));
     if (!P.tc_err.p) {
-        TFMM_CUDA_CHECK(cudaMalloc(&P.tc_err.p, sizeof(int)));
+        TFMM_CUDA_CHECK(device_malloc(&P.tc_err.p, sizeof(int)));
         TFMM_CUDA_CHECK(cudaMemset(P.tc_err.p, 0, sizeof(int)));
     }
 }
@@ -1159,8 +1159,8 @@ void upload_tc_stage(TcStagePlan& st, const std::vector<TcProb>& probs, const st
         st.max_kt = std::max(st.max_kt, kt);
         st.max_bn = std::max(st.max_bn, p.BN);
     }
-    TFMM_CUDA_CHECK(cudaMalloc(&st.d_probs, sizeof(TcProb) * std::max<size_t>(probs.size(), 1)));
-    TFMM_CUDA_CHECK(cudaMalloc(&st.d_tiles, sizeof(MrTile) * std::max<size_t>(tiles.size(), 1)));
+    TFMM_CUDA_CHECK(device_malloc(&st.d_probs, sizeof(TcProb) * std::max<size_t>(probs.size(), 1)));
+    TFMM_CUDA_CHECK(device_malloc(&st.d_tiles, sizeof(MrTile) * std::max<size_t>(tiles.size(), 1)));
     TFMM_CUDA_CHECK(cudaMemcpy(st.d_probs, probs.data(), sizeof(TcProb) * probs.size(), cudaMemcpyHostToDevice));
     TFMM_CUDA_CHECK(cudaMemcpy(st.d_tiles, tiles.data(), sizeof(MrTile) * tiles.size(), cudaMemcpyHostToDevice));
 }
@@ -1239,8 +1239,8 @@ void plan_fused34(const Plan& P, TcPlan& M, const bf16* F, const std::vector<TcI
     std::vector<F34Tile> tiles;
     for (int q : order)
         for (int r0 = 0; r0 < R; r0 += nr_of[q]) tiles.push_back(F34Tile{q, r0, std::min(nr_of[q], R - r0)});
-    TFMM_CUDA_CHECK(cudaMalloc(&M.f34_items.p, sizeof(F34Item) * items.size()));
-    TFMM_CUDA_CHECK(cudaMalloc(&M.f34_tiles.p, sizeof(F34Tile) * tiles.size()));
+    TFMM_CUDA_CHECK(device_malloc(&M.f34_items.p, sizeof(F34Item) * items.size()));
+    TFMM_CUDA_CHECK(device_malloc(&M.f34_tiles.p, sizeof(F34Tile) * tiles.size()));
     TFMM_CUDA_CHECK(cudaMemcpy(M.f34_items.p, items.data(), sizeof(F34Item) * items.size(), cudaMemcpyHostToDevice));
     TFMM_CUDA_CHECK(cudaMemcpy(M.f34_tiles.p, tiles.data(), sizeof(F34Tile) * tiles.size(), cudaMemcpyHostToDevice));
     M.f34_ntiles = (int)tiles.size();
@@ -1295,8 +1295,8 @@ void plan_dg1a(const Plan& P, TcPlan& M, const bf16* F, const std::vector<TcItem
     const int npairs = np * R;
     for (size_t q = 0; q < P.items.size(); ++q)
         for (int p0 = 0; p0 < npairs; p0 += NP) tiles.push_back(D1Tile{(int)q, p0});
-    TFMM_CUDA_CHECK(cudaMalloc(&M.dg1a_items.p, sizeof(D1Item) * items.size()));
-    TFMM_CUDA_CHECK(cudaMalloc(&M.dg1a_tiles.p, sizeof(D1Tile) * tiles.size()));
+    TFMM_CUDA_CHECK(device_malloc(&M.dg1a_items.p, sizeof(D1Item) * items.size()));
+    TFMM_CUDA_CHECK(device_malloc(&M.dg1a_tiles.p, sizeof(D1Tile) * tiles.size()));
     TFMM_CUDA_CHECK(cudaMemcpy(M.dg1a_items.p, items.data(), sizeof(D1Item) * items.size(), cudaMemcpyHostToDevice));
     TFMM_CUDA_CHECK(cudaMemcpy(M.dg1a_tiles.p, tiles.data(), sizeof(D1Tile) * tiles.size(), cudaMemcpyHostToDevice));
     M.dg1a_ntiles = (int)tiles.size();
@@ -1353,7 +1353,7 @@ TcPlan* get_tc_plan(Plan& P, int R, int T, cudaStream_t s) {
         for (int b = 0; b < NB; ++b) sz[b] = (sz[b] + 63) & ~int64_t(63);
     }
     for (int b = 0; b < NB; ++b) {
-        TFMM_CUDA_CHECK(cudaMalloc(&M.buf[b], sizeof(bf16) * std::max<int64_t>(sz[b], 1)));
+        TFMM_CUDA_CHECK(device_malloc(&M.buf[b], sizeof(bf16) * std::max<int64_t>(sz[b], 1)));
         TFMM_CUDA_CHECK(cudaMemset(M.buf[b], 0, sizeof(bf16) * std::max<int64_t>(sz[b], 1)));
     }
     bf16* X = reinterpret_cast<bf16*>(M.buf[BX]);

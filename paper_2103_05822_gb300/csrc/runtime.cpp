@@ -184,7 +184,7 @@ std::unique_ptr<tfmm_plan> load_plan(const char* path, cudaStream_t s) {
         }
     upload_common(P, s);
     double2* arena = nullptr;
-    TFMM_CUDA_CHECK(cudaMalloc(&arena, sizeof(double2) * total));
+    TFMM_CUDA_CHECK(device_malloc(&arena, sizeof(double2) * total));
     P.f64_arenas.push_back(arena);
     P.f64.assign((size_t)P.G * 2, HostFactors64{});
     std::vector<double2> buf;
@@ -206,7 +206,7 @@ std::unique_ptr<tfmm_plan> load_plan(const char* path, cudaStream_t s) {
     bad(std::memcmp(tail, kTrailer, 8) != 0, "trailer");
     if (std::fgetc(F.f) != EOF) fail(TFMM_IO, "trailing bytes after the checkpoint: " + F.path);
     if (P.has_geometry) {
-        TFMM_CUDA_CHECK(cudaMalloc(&P.d_geom, sizeof(RwgGeom) * P.N));
+        TFMM_CUDA_CHECK(device_malloc(&P.d_geom, sizeof(RwgGeom) * P.N));
         TFMM_CUDA_CHECK(cudaMemcpyAsync(P.d_geom, P.geom.data(), sizeof(RwgGeom) * P.N, cudaMemcpyHostToDevice, s));
     }
     pack_factors_fp32(P, s);
@@ -372,6 +372,7 @@ tfmm_status tfmm_plan_tuning_get(const tfmm_plan* plan, tfmm_tuning* t) {
         t->mrhs_precision = P.params.mrhs_precision;
         t->tc_f34_n1 = P.tc_f34_n1;
         t->tc_dg1a_pairs = P.tc_dg1a_pairs;
+        t->single_rhs_split = P.tuning.split;
         t->agg_ms = P.tuned_ms[0];
         t->dis_ms = P.tuned_ms[1];
     });
@@ -385,6 +386,8 @@ tfmm_status tfmm_plan_tuning_set(tfmm_plan* plan, const tfmm_tuning* t, void* st
                      "tc_f34_n1 must be 0 or a multiple of 16 in 16..256");
         TFMM_REQUIRE(t->tc_dg1a_pairs == 0 || t->tc_dg1a_pairs == 64 || t->tc_dg1a_pairs == 128,
                      "tc_dg1a_pairs must be 0, 64 or 128");
+        TFMM_REQUIRE(t->single_rhs_split >= 0 && t->single_rhs_split <= 2,
+                     "single_rhs_split must be 0 (automatic), 1 (always) or 2 (never)");
         if (t->tc_f34_n1 != plan->p.tc_f34_n1 || t->tc_dg1a_pairs != plan->p.tc_dg1a_pairs) {
             TFMM_REQUIRE(plan->p.live_graphs == 0, "destroy the plan's graphs before changing tile shapes");
             plan->p.tc_f34_n1 = t->tc_f34_n1;
@@ -394,6 +397,7 @@ tfmm_status tfmm_plan_tuning_set(tfmm_plan* plan, const tfmm_tuning* t, void* st
         HotTuning h;
         h.agg_threads = t->agg_threads; h.agg_ctas_per_sm = t->agg_ctas_per_sm; h.agg_order = t->agg_order;
         h.dis_threads = t->dis_threads; h.dis_ctas_per_sm = t->dis_ctas_per_sm; h.dis_order = t->dis_order;
+        h.split = t->single_rhs_split;
         const HotTuning old = plan->p.tuning;
         const bool was_ok = plan->p.hot_ok;
         configure_hot(plan->p, h, (cudaStream_t)stream);
@@ -420,9 +424,9 @@ tfmm_status tfmm_autotune(tfmm_plan* plan, int32_t R, double budget_ms, int32_t 
         };
         Scratch w;
         const size_t xb = sizeof(float2) * (size_t)P.N * R, sb = sizeof(float2) * (size_t)R * P.G * 2 * P.n_dir;
-        TFMM_CUDA_CHECK(cudaMalloc(&w.x.p, xb));
-        TFMM_CUDA_CHECK(cudaMalloc(&w.spec.p, sb));
-        TFMM_CUDA_CHECK(cudaMalloc(&w.y.p, xb));
+        TFMM_CUDA_CHECK(device_malloc(&w.x.p, xb));
+        TFMM_CUDA_CHECK(device_malloc(&w.spec.p, sb));
+        TFMM_CUDA_CHECK(device_malloc(&w.y.p, xb));
         // any finite data times the same: bytes 0x3c give floats of about 0.0115
         TFMM_CUDA_CHECK(cudaMemsetAsync(w.x.p, 0x3c, xb, s));
         TFMM_CUDA_CHECK(cudaMemsetAsync(w.spec.p, 0x3c, sb, s));

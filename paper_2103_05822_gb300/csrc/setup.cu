@@ -72,7 +72,7 @@ struct DevBuf {
     void alloc(size_t b) {
         release();
         if (b == 0) return;
-        TFMM_CUDA_CHECK(cudaMalloc(&p, b));
+        TFMM_CUDA_CHECK(device_malloc(&p, b));
         bytes = b;
     }
     void release() {
@@ -772,7 +772,7 @@ void hosvd_batch(Plan& P, std::vector<Tensor>& T, std::vector<std::unique_ptr<Wo
         rbmax = std::max(rbmax, rb);
     }
     double2* arena = nullptr;
-    TFMM_CUDA_CHECK(cudaMalloc(&arena, sizeof(double2) * std::max<int64_t>(f_tot, 1)));
+    TFMM_CUDA_CHECK(device_malloc(&arena, sizeof(double2) * std::max<int64_t>(f_tot, 1)));
     P.f64_arenas.push_back(arena);
     // QR workspace per worker
     int qr_lw = 1;
@@ -903,7 +903,7 @@ void build_tucker_setup(Plan& P, const Mesh& M, cudaStream_t s) {
     const int nq = prm.quad_order * prm.quad_order;
 
     // geometry and directions
-    TFMM_CUDA_CHECK(cudaMalloc(&P.d_geom, sizeof(RwgGeom) * std::max<int64_t>(P.N, 1)));
+    TFMM_CUDA_CHECK(device_malloc(&P.d_geom, sizeof(RwgGeom) * std::max<int64_t>(P.N, 1)));
     TFMM_CUDA_CHECK(cudaMemcpyAsync(P.d_geom, P.geom.data(), sizeof(RwgGeom) * P.N, cudaMemcpyHostToDevice, s));
     const std::vector<double> dirs = direction_table(P);
     DevBuf d_dirs(sizeof(double) * dirs.size());
@@ -912,7 +912,7 @@ void build_tucker_setup(Plan& P, const Mesh& M, cudaStream_t s) {
     // dense FP32 copy
     if (keep_dense) {
         P.dense_elems = (int64_t)P.ld_dir * P.N * 2;
-        TFMM_CUDA_CHECK(cudaMalloc(&P.d_dense, sizeof(float2) * std::max<int64_t>(P.dense_elems, 1)));
+        TFMM_CUDA_CHECK(device_malloc(&P.d_dense, sizeof(float2) * std::max<int64_t>(P.dense_elems, 1)));
     }
 
     int nworkers = 8;

@@ -10,6 +10,10 @@
 #include <string>
 #include <tuple>
 
+#include <atomic>
+
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
 
 namespace tfmm {
@@ -24,11 +28,11 @@ void upload_common(Plan& P, cudaStream_t s) {
     TFMM_CUDA_CHECK(cudaGetDevice(&dev));
     TFMM_CUDA_CHECK(cudaDeviceGetAttribute(&P.num_sms, cudaDevAttrMultiProcessorCount, dev));
     std::vector<int> ids(P.grp_rwg.begin(), P.grp_rwg.end());
-    TFMM_CUDA_CHECK(cudaMalloc(&P.d_grp_rwg, sizeof(int) * std::max<int64_t>(P.N, 1)));
+    TFMM_CUDA_CHECK(device_malloc(&P.d_grp_rwg, sizeof(int) * std::max<int64_t>(P.N, 1)));
     TFMM_CUDA_CHECK(cudaMemcpyAsync(P.d_grp_rwg, ids.data(), sizeof(int) * P.N, cudaMemcpyHostToDevice, s));
-    TFMM_CUDA_CHECK(cudaMalloc(&P.d_weights, sizeof(float) * P.n_dir));
+    TFMM_CUDA_CHECK(device_malloc(&P.d_weights, sizeof(float) * P.n_dir));
     TFMM_CUDA_CHECK(cudaMemcpyAsync(P.d_weights, P.weights.data(), sizeof(float) * P.n_dir, cudaMemcpyHostToDevice, s));
-    TFMM_CUDA_CHECK(cudaMalloc(&P.d_counters, sizeof(unsigned) * 16));
+    TFMM_CUDA_CHECK(device_malloc(&P.d_counters, sizeof(unsigned) * 16));
     TFMM_CUDA_CHECK(cudaMemsetAsync(P.d_counters, 0, sizeof(unsigned) * 16, s));
     TFMM_CUDA_CHECK(cudaStreamSynchronize(s));
 }
@@ -180,7 +184,14 @@ Engine engine_for(const Plan& P, int R, int* terms) {
     return Engine::chain;
 }
 
+// An NVTX range around one hot-path call (seen by profilers, free otherwise).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 void run_aggregate(Plan& P, const float2* x, int R, int64_t ldx, float2* spec, cudaStream_t s) {
+    NvtxRange nvtx("tfmm_aggregate");
     int T = 0;
     switch (engine_for(P, R, &T)) {
         case Engine::tc: launch_tc_aggregate(P, T, x, R, ldx, spec, s); break;
@@ -191,6 +202,7 @@ void run_aggregate(Plan& P, const float2* x, int R, int64_t ldx, float2* spec, c
 
 void run_disaggregate(Plan& P, const float2* spec, int R, int weights, float2 beta, float2* y, int64_t ldy,
                       cudaStream_t s) {
+    NvtxRange nvtx("tfmm_disaggregate");
     int T = 0;
     switch (engine_for(P, R, &T)) {
         case Engine::tc: launch_tc_disaggregate(P, T, spec, R, weights, beta, y, ldy, s); break;
@@ -209,9 +221,33 @@ void check_hot(const Plan& P, const void* a, const void* b, int R, int64_t ld) {
 }  // namespace
 }  // namespace tfmm
 
+namespace tfmm {
+
+namespace {
+// Allocations left before the one the test hook fails (0: disarmed).
+std::atomic<int64_t> g_fail_alloc_in{0};
+}  // namespace
+
+cudaError_t device_malloc_bytes(void** p, size_t bytes) {
+    if (g_fail_alloc_in.load() > 0 && g_fail_alloc_in.fetch_sub(1) == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+}  // namespace tfmm
+
 using namespace tfmm;
 
 extern "C" {
+
+tfmm_status tfmm_test_fail_allocation(int64_t nth) {
+    return guarded([&] {
+        TFMM_REQUIRE(nth >= 0, "nth must be >= 0");
+        g_fail_alloc_in.store(nth);
+    });
+}
 
 const char* tfmm_last_error(void) { return last_error().c_str(); }
 
@@ -374,7 +410,7 @@ tfmm_status tfmm_plan_from_tucker(int64_t n_rwg, int32_t n_groups, int32_t n_the
             }
         }
         double2* arena = nullptr;
-        TFMM_CUDA_CHECK(cudaMalloc(&arena, sizeof(double2) * pos));
+        TFMM_CUDA_CHECK(device_malloc(&arena, sizeof(double2) * pos));
         P.f64_arenas.push_back(arena);
         TFMM_CUDA_CHECK(cudaMemcpyAsync(arena, src, sizeof(double2) * pos, cudaMemcpyHostToDevice, s));
         pos = 0;
@@ -401,7 +437,7 @@ tfmm_status tfmm_plan_set_dense(tfmm_plan* plan, const tfmm_cdouble* tensors, vo
         cudaStream_t s = (cudaStream_t)stream;
         if (!P.d_dense) {
             P.dense_elems = (int64_t)P.ld_dir * P.N * 2;
-            TFMM_CUDA_CHECK(cudaMalloc(&P.d_dense, sizeof(float2) * P.dense_elems));
+            TFMM_CUDA_CHECK(device_malloc(&P.d_dense, sizeof(float2) * P.dense_elems));
         }
         TFMM_CUDA_CHECK(cudaMemsetAsync(P.d_dense, 0, sizeof(float2) * P.dense_elems, s));
         const double2* src = reinterpret_cast<const double2*>(tensors);
@@ -409,7 +445,7 @@ tfmm_status tfmm_plan_set_dense(tfmm_plan* plan, const tfmm_cdouble* tensors, vo
         double2* tmp = nullptr;
         int64_t max_e = 0;
         for (int g = 0; g < P.G; ++g) max_e = std::max<int64_t>(max_e, (P.grp_off[g + 1] - P.grp_off[g]) * P.n_dir);
-        TFMM_CUDA_CHECK(cudaMalloc(&tmp, sizeof(double2) * max_e));
+        TFMM_CUDA_CHECK(device_malloc(&tmp, sizeof(double2) * max_e));
         struct Free { double2* p; ~Free() { cudaFree(p); } } fr{tmp};
         for (int g = 0; g < P.G; ++g)
             for (int al = 0; al < 2; ++al) {
@@ -582,9 +618,9 @@ tfmm_status tfmm_matvec_host(tfmm_plan* plan, const tfmm_cfloat* x_host, tfmm_cf
             cudaFree(P.d_ws_x); cudaFree(P.d_ws_spec); cudaFree(P.d_ws_y);
             P.d_ws_x = P.d_ws_spec = P.d_ws_y = nullptr;
             P.ws_R = 0;
-            TFMM_CUDA_CHECK(cudaMalloc(&P.d_ws_x, sizeof(float2) * P.N * R));
-            TFMM_CUDA_CHECK(cudaMalloc(&P.d_ws_y, sizeof(float2) * P.N * R));
-            TFMM_CUDA_CHECK(cudaMalloc(&P.d_ws_spec, sizeof(float2) * (int64_t)R * P.G * 2 * P.n_dir));
+            TFMM_CUDA_CHECK(device_malloc(&P.d_ws_x, sizeof(float2) * P.N * R));
+            TFMM_CUDA_CHECK(device_malloc(&P.d_ws_y, sizeof(float2) * P.N * R));
+            TFMM_CUDA_CHECK(device_malloc(&P.d_ws_spec, sizeof(float2) * (int64_t)R * P.G * 2 * P.n_dir));
             P.ws_R = R;
         }
         TFMM_CUDA_CHECK(cudaMemcpyAsync(P.d_ws_x, x_host, sizeof(float2) * P.N * R, cudaMemcpyHostToDevice, s));
@@ -607,6 +643,19 @@ tfmm_status tfmm_planewave(const tfmm_plan* plan, const double* khat, const doub
         TFMM_REQUIRE(plan && khat && pol && V, "null argument");
         TFMM_REQUIRE(R >= 1, "R must be >= 1");
         planewave_rhs(plan->p, khat, pol, R, reinterpret_cast<float2*>(V), (cudaStream_t)stream);
+    });
+}
+
+tfmm_status tfmm_translate(tfmm_plan* plan, const tfmm_cfloat* spectra_out, int32_t R, tfmm_cfloat* spectra_in,
+                           void* stream) {
+    return guarded([&] {
+        TFMM_REQUIRE(plan, "null plan");
+        TFMM_REQUIRE(spectra_out && spectra_in, "null buffer");
+        TFMM_REQUIRE(spectra_out != spectra_in, "spectra_out and spectra_in must not be the same buffer");
+        TFMM_REQUIRE(R >= 1 && R <= plan->p.params.max_rhs, "R must be in 1..max_rhs");
+        NvtxRange nvtx("tfmm_translate");
+        launch_translate(plan->p, reinterpret_cast<const float2*>(spectra_out), R, reinterpret_cast<float2*>(spectra_in),
+                         (cudaStream_t)stream);
     });
 }
 

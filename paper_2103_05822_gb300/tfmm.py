@@ -26,10 +26,10 @@ EXPORTED = [
     "tfmm_plan_group", "tfmm_plan_members", "tfmm_plan_centres", "tfmm_plan_quadrature",
     "tfmm_plan_export_factors", "tfmm_plan_farfield", "tfmm_plan_destroy",
     "tfmm_aggregate", "tfmm_disaggregate", "tfmm_aggregate_dense", "tfmm_disaggregate_dense",
-    "tfmm_matvec_host", "tfmm_planewave", "tfmm_planewave_noalloc", "tfmm_plan_set_mrhs_precision",
+    "tfmm_matvec_host", "tfmm_planewave", "tfmm_planewave_noalloc", "tfmm_plan_set_mrhs_precision", "tfmm_translate",
     "tfmm_sync", "tfmm_plan_rwg_perm", "tfmm_plan_save", "tfmm_plan_load",
     "tfmm_graph_capture", "tfmm_graph_launch", "tfmm_graph_destroy",
-    "tfmm_plan_tuning_get", "tfmm_plan_tuning_set", "tfmm_autotune",
+    "tfmm_plan_tuning_get", "tfmm_plan_tuning_set", "tfmm_autotune", "tfmm_test_fail_allocation",
 ]
 
 
@@ -77,11 +77,12 @@ class Tuning(ctypes.Structure):
         ("agg_threads", ctypes.c_int32), ("agg_ctas_per_sm", ctypes.c_int32), ("agg_order", ctypes.c_int32),
         ("dis_threads", ctypes.c_int32), ("dis_ctas_per_sm", ctypes.c_int32), ("dis_order", ctypes.c_int32),
         ("agg_blocks", ctypes.c_int32), ("dis_blocks", ctypes.c_int32), ("mrhs_precision", ctypes.c_int32),
-        ("tc_f34_n1", ctypes.c_int32), ("tc_dg1a_pairs", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1),
+        ("tc_f34_n1", ctypes.c_int32), ("tc_dg1a_pairs", ctypes.c_int32), ("single_rhs_split", ctypes.c_int32),
         ("agg_ms", ctypes.c_double), ("dis_ms", ctypes.c_double),
     ]
     _names = ("agg_threads", "agg_ctas_per_sm", "agg_order", "dis_threads", "dis_ctas_per_sm", "dis_order",
-              "agg_blocks", "dis_blocks", "mrhs_precision", "tc_f34_n1", "tc_dg1a_pairs", "agg_ms", "dis_ms")
+              "agg_blocks", "dis_blocks", "mrhs_precision", "tc_f34_n1", "tc_dg1a_pairs", "single_rhs_split",
+              "agg_ms", "dis_ms")
 
     def as_dict(self):
         return {k: getattr(self, k) for k in self._names}
@@ -124,6 +125,7 @@ def load():
         "tfmm_matvec_host": [P, P, P, I32, I32, P],
         "tfmm_planewave": [P, P, P, I32, P, P],
         "tfmm_planewave_noalloc": [P, P, P, I32, P, P],
+        "tfmm_translate": [P, P, I32, P, P],
         "tfmm_plan_set_mrhs_precision": [P, I32],
         "tfmm_sync": [P, P],
         "tfmm_plan_rwg_perm": [P, P, P],
@@ -135,6 +137,7 @@ def load():
         "tfmm_plan_tuning_get": [P, P],
         "tfmm_plan_tuning_set": [P, P, P],
         "tfmm_autotune": [P, I32, D, I32, P, P],
+        "tfmm_test_fail_allocation": [I64],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -386,6 +389,13 @@ def tfmm_matvec_host(plan, x_host, y_host, R=1, dense=False, stream=None):
     _check(load().tfmm_matvec_host(plan.handle, ptr(x_host), ptr(y_host), R, int(bool(dense)), _stream(stream)))
 
 
+def tfmm_translate(plan, spectra_out, spectra_in, R=None, stream=None):
+    """Incoming spectra of every group from the outgoing ones (far box pairs), (R, G, 2, N_dir) complex64."""
+    if R is None:
+        R = spectra_out.shape[0]
+    _check(load().tfmm_translate(plan.handle, _dev_ptr(spectra_out), int(R), _dev_ptr(spectra_in), _stream(stream)))
+
+
 def tfmm_planewave(plan, khat, pol, V, stream=None):
     k = np.ascontiguousarray(khat, np.float64).reshape(-1, 3)
     p = np.ascontiguousarray(pol, np.float64).reshape(-1, 3)
@@ -485,3 +495,8 @@ def tfmm_autotune(plan, R=1, budget_ms=2000.0, allow_two_term=False, stream=None
     _check(load().tfmm_autotune(plan.handle, int(R), float(budget_ms), int(bool(allow_two_term)), _stream(stream),
                                 ctypes.byref(t)))
     return t.as_dict()
+
+
+def tfmm_test_fail_allocation(nth):
+    """Test hook: the nth device allocation the library makes from now on fails (0 disarms)."""
+    _check(load().tfmm_test_fail_allocation(int(nth)))

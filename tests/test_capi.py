@@ -205,3 +205,11 @@ def test_well_formed_checkpoint_passes_the_header_checks(lib, tmp_path):
         with pytest.raises(tfmm.TfmmError) as e:
             tfmm.tfmm_plan_load(str(f), stream=0)
         assert e.value.status == tfmm.CUDA, str(e.value)
+
+
+def test_allocation_failure_hook_arguments(lib):
+    """The error-path test hook accepts nth >= 0 (0 disarms) and refuses negative counts."""
+    tfmm.tfmm_test_fail_allocation(0)
+    with pytest.raises(tfmm.TfmmError) as e:
+        tfmm.tfmm_test_fail_allocation(-1)
+    assert e.value.status == tfmm.INVALID_ARG

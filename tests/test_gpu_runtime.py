@@ -188,8 +188,9 @@ def test_graph_replays_equal_eager_calls(synth):
 def test_every_launch_shape_matches_oracle(synth, threads, ctas, order):
     tfmm = _tfmm()
     plan = synth["plan"]
+    # the persistent kernels (this few-group plan takes the split path by default)
     tfmm.tfmm_plan_tuning_set(plan, agg_threads=threads, agg_ctas_per_sm=ctas, agg_order=order,
-                              dis_threads=threads, dis_ctas_per_sm=ctas, dis_order=order)
+                              dis_threads=threads, dis_ctas_per_sm=ctas, dis_order=order, single_rhs_split=2)
     t = tfmm.tfmm_plan_tuning_get(plan)
     assert (t["agg_threads"], t["agg_order"], t["dis_threads"], t["dis_order"]) == (threads, order, threads, order)
     assert t["agg_blocks"] >= 1 and t["dis_blocks"] >= 1
@@ -204,6 +205,34 @@ def test_every_launch_shape_matches_oracle(synth, threads, ctas, order):
             assert _rel(s[0, g, a], ref[g, a]) <= 1e-5
     refy = apply.disaggregate_all(synth["T"], synth["members"], gv[0], n, synth["w"])
     assert _rel(y, refy) <= 1e-5
+
+
+def test_split_path_matches_persistent_kernels_and_oracle(synth):
+    """Few groups: each stage as three launches spreading every item over many CTAs
+    (row blocks of U_beta / C_(3), column blocks, one CTA per item for the theta / phi
+    steps).  Same results as the persistent kernels (FP32 rounding) and the oracle."""
+    tfmm = _tfmm()
+    plan = synth["plan"]
+    G, nd, n = len(synth["members"]), synth["nt"] * synth["npf"], synth["n_rwg"]
+    xv = torch.from_numpy(complex_gaussian(n, 72).astype(np.complex64)).cuda()
+    gv = torch.from_numpy(complex_gaussian((1, G, 2, nd), 73).astype(np.complex64)).cuda()
+    out = {}
+    for split in (1, 2):
+        tfmm.tfmm_plan_tuning_set(plan, single_rhs_split=split)
+        assert tfmm.tfmm_plan_tuning_get(plan)["single_rhs_split"] == split
+        out[split] = _agg_dis(plan, xv, gv)
+    tfmm.tfmm_plan_tuning_set(plan, single_rhs_split=0)
+    ref = apply.aggregate_all(synth["T"], synth["members"], xv.cpu().numpy().astype(np.complex128))
+    refy = apply.disaggregate_all(synth["T"], synth["members"], gv.cpu().numpy()[0].astype(np.complex128), n, synth["w"])
+    for split in (1, 2):
+        s_, y_ = out[split]
+        for g in range(G):
+            for a in range(2):
+                assert _rel(s_[0, g, a], ref[g, a]) <= 1e-5, (split, g, a)
+        assert _rel(y_, refy) <= 1e-5, split
+    assert _rel(out[1][0], out[2][0]) <= 1e-5 and _rel(out[1][1], out[2][1]) <= 1e-5
+    with pytest.raises(tfmm.TfmmError):
+        tfmm.tfmm_plan_tuning_set(plan, single_rhs_split=3)
 
 
 def test_tuning_rejects_bad_shapes(synth):

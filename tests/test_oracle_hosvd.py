@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
-from oracle import hosvd
+from oracle import hosvd, svd
 from paper_2103_05822_gb300.inputs import icosphere
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")
@@ -111,7 +111,7 @@ def test_tolerance_is_split_over_three_modes():
 
 @pytest.mark.slow
 def test_ranks_match_paper_table_iv_order_of_magnitude():
-    """A 2-lambda box on a 30-lambda sphere at L = 37, gamma = 1e-6 (Table IV: 25, 29, 175)."""
+    """A 2-lambda box on a 30-lambda sphere at L = 37, gamma = 1e-6 (Table IV: Tucker 25, 29, 175; SVD 168)."""
     gold = json.load(open(GOLDEN))["sphere_ranks_2lambda"]
     v, f = icosphere(30.0, 180)
     # keep only triangles near one box (a patch around a point of the sphere)
@@ -147,4 +147,7 @@ def test_ranks_match_paper_table_iv_order_of_magnitude():
         assert 0.7 * gold["r_theta"] <= rt <= 1.3 * gold["r_theta"], T.ranks
         assert 0.7 * gold["r_phi"] <= rp <= 1.4 * gold["r_phi"], T.ranks
         assert 0.6 * gold["r_beta"] <= rb <= 1.5 * gold["r_beta"] * max(1.0, scale_b), T.ranks
-        print("ranks", len(ids), T.ranks)
+        # the SVD comparator of the same box (Table IV, SVD column): just below the Tucker r_beta
+        rs = svd.truncated_svd(A, gold["tol"]).rank
+        assert rs <= rb and 0.6 * gold["svd_r_beta"] <= rs <= 1.5 * gold["svd_r_beta"] * max(1.0, scale_b), rs
+        print("ranks", len(ids), T.ranks, "svd", rs)
