@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--svd", action="store_true",
                     help="also build the truncated-SVD comparator (Sec. II.C) of the workload and time it: "
                          "the Table III analogue (dense / SVD / Tucker memory and ms) on one GPU")
+    ap.add_argument("--tuning", default="",
+                    help="KEY=VALUE[,KEY=VALUE...] fields of tfmm_tuning set on the plan before timing "
+                         "(e.g. dis_threads=384,dis_ctas_per_sm=2)")
     ap.add_argument("--mrhs-precision", type=int, default=None,
                     help="R > 1: 0 FP32 CUDA cores, 2 / 3 tensor cores with 2- / 3-term split BF16 (default 3)")
     return ap.parse_args()
@@ -289,6 +292,20 @@ def run_reference(args, w, world, rank):
 
 
 # --------------------------------------------------------------------- ours
+def launches_per_step(tfmm, plan, R, dev):
+    """Kernels one aggregate + disaggregate pair launches: one persistent kernel per stage
+    for one RHS (three per stage on the split path, taken by plans with fewer work items
+    than twice the SMs), the tensor-core chain for many (operand prep and four kernels
+    for aggregation, four for disaggregation)."""
+    import torch
+    t = tfmm.tfmm_plan_tuning_get(plan)
+    if R == 1:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        split = t["single_rhs_split"] == 1 or (t["single_rhs_split"] == 0 and 2 * plan.info["n_groups"] < 2 * sms)
+        return 6 if split else 2
+    return 8
+
+
 def traffic_record(kernel, factor_bytes):
     """DRAM bytes per launch from a committed ncu capture (scaled by the factor bytes streamed),
     if the kernel source is unchanged since."""
@@ -334,6 +351,9 @@ def run_ours(args, w, world, rank, local):
     stream = torch.cuda.current_stream()
     plan = tfmm.tfmm_plan_create(mesh, prm, stream=stream)
     setup_s = time.perf_counter() - t0
+    if args.tuning:
+        kv = dict(item.split("=") for item in args.tuning.split(","))
+        tfmm.tfmm_plan_tuning_set(plan, stream=stream, **{k.strip(): int(v) for k, v in kv.items()})
     info = plan.info
     N, G, nd = info["n_rwg"], info["n_groups"], info["n_dir"]
 
@@ -631,8 +651,9 @@ def run_ours(args, w, world, rank, local):
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 8 * N * R, "d2h_bytes_per_step": 8 * N * R},
-            "gpu_launches": (2 if R == 1 else 8) * args.steps,
+            "gpu_launches": launches_per_step(tfmm, plan, R, dev) * args.steps,
             "nrhs": R, "graph": bool(args.graph), "mrhs_precision": mp if R > 1 else None,
+            "tuning": tfmm.tfmm_plan_tuning_get(plan),
             "clocks": clocks.summary(),
         }
         print(json.dumps(line), flush=True)

@@ -154,6 +154,14 @@ struct FusedShape {
     size_t smem = 0;         // dynamic shared memory per CTA
 };
 
+// DG1a or DG1b with the BF16 terms of the factor stacked along N (tc_cat_kernel)
+struct CatPlan {
+    bool on = false;
+    int K = 0, K16 = 0, n8max = 0, tcols = 0, ntiles = 0;
+    size_t smem = 0;
+    DeviceBuffer items, tiles;
+};
+
 struct TcPlan {             // per (R, terms): problem lists of the 8 steps and scratch planes
     int R = 0, T = 0;
     TcStagePlan st[8];
@@ -168,6 +176,7 @@ struct TcPlan {             // per (R, terms): problem lists of the 8 steps and 
     int dg1a_K = 0, dg1a_NP = 0, dg1a_AR = 0, dg1a_ntiles = 0;
     size_t dg1a_smem = 0;
     DeviceBuffer dg1a_items, dg1a_tiles;
+    CatPlan cat1a, cat1b;   // the stacked-term forms of DG1a / DG1b, when they fit
     // per item: element offsets of its M' and V'' / P'' scratch planes (for re-planning)
     std::vector<int64_t> m_off, v_off;
     ~TcPlan();

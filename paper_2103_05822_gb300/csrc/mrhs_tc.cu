@@ -946,6 +946,266 @@ __global__ void __launch_bounds__(D1_THREADS) tc_dg1a_kernel(const TcCtx c, cons
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(tcols));
 }
 
+// --------------------------------- narrow-N steps with the BF16 terms stacked along N
+// DG1a  P'_r[i_phi][a] = sum_theta conj(W g_r)[theta][i_phi] U_theta[theta][a]   (Fig. 3b
+//       step 1, first factor): rows m = i_phi + n_phi r on the TMEM lanes, A from the FP32
+//       spectra (weighted, conjugated and split here), out the P'' planes [a + r_t r][i_phi];
+// DG1b  H'_r[a][b] = sum_phi P'_r[i_phi][a] U_phi[i_phi][b]   (second factor): rows
+//       m = a + r_t r, A the P'' planes, out the H planes [r][a + r_t b] that DG2 reads.
+// N (r_theta or r_phi) is narrow, so the term products share MMAs: B stacks the BF16
+// terms of the factor along N, Bpos = [Re_0 Im_0 Re_1 Im_1 ...] and Bneg = [-Im_0 Re_0
+// -Im_1 Re_1 ...] (n8 = r8(rank) rows each), and term p of A multiplies the first T - p
+// term pairs of B into the accumulator columns from 2 p n8 on,
+//   A_p,re Bpos + A_p,im Bneg  ->  [L_p | ... | L_(T-1)],
+// so that L_q (2 n8 columns, re | im) collects the products whose term orders add up
+// to q: the leading hi x hi product alone in L_0, the corrections in their own
+// accumulators, and the result is (L_2 + L_1) + L_0.  A K step of 16 takes 2T MMAs of
+// N = 2 (T - p) n8 columns instead of 4 n_products narrow ones.  B is split here from
+// the FP32 factor.  The epilogue writes the output planes straight from TMEM (one row
+// per thread, consecutive rows on consecutive lanes).
+struct CatItem {
+    const float2* fac;               // U_theta (DG1a) or U_phi (DG1b): K x rank, column-major (FP32)
+    const bf16* a; int64_t a_ld, a_ps;  // DG1b: P'' planes [a + r_t r][i_phi]
+    bf16* out; int64_t o_ld, o_ps;   // P'' (DG1a) or H (DG1b) planes
+    int g, alpha, rt, rank, M;       // rank = N of this item; M = rows (n_phi R or r_t R)
+};
+
+constexpr int CAT_THREADS = 256;
+constexpr int CAT_ITER = 4;  // DG1a A loads per thread: 128 rows x K16 / 8 <= 4 x CAT_THREADS (host check)
+enum { CAT_DG1A = 0, CAT_DG1B = 1 };
+
+// byte offset of 16-byte chunk kc of row `row` in the canonical no-swizzle K-major layout
+__device__ __forceinline__ int canon_off(int row, int kc, uint32_t sbo) {
+    return (row >> 3) * (int)sbo + kc * 128 + (row & 7) * 16;
+}
+
+// DG1a A, rows p0 .. p0 + 127 = (i_phi, r) pairs, depth theta: conj(W g) loaded into
+// registers (zero past n_theta and the item's rows)
+__device__ __forceinline__ void cat_load_g(float2 (&v)[CAT_ITER][8], const TcCtx& c, const CatItem& it, int p0,
+                                           int kc8, int n_phi) {
+    const int nt = c.n_theta, ntask = TBM * kc8;
+#pragma unroll
+    for (int u = 0; u < CAT_ITER; ++u) {
+        const int task = threadIdx.x + u * CAT_THREADS, i = task / kc8, kc = task % kc8, p = p0 + i;
+        const bool row_ok = task < ntask && p < it.M;
+        const int ip = row_ok ? p % n_phi : 0, r = row_ok ? p / n_phi : 0;
+        const int64_t o = (((int64_t)r * c.G + it.g) * 2 + it.alpha) * c.n_dir + (int64_t)nt * ip;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int th = kc * 8 + e;
+            v[u][e] = make_float2(0.f, 0.f);
+            if (row_ok && th < nt) {
+                const float2 g = __ldg(c.spec_in + o + th);
+                const float wt = c.w ? __ldg(c.w + th + (int64_t)nt * ip) : 1.0f;
+                v[u][e] = make_float2(wt * g.x, -wt * g.y);
+            }
+        }
+    }
+}
+
+// the loaded DG1a A values, split into 2T planes of the canonical layout
+template <int T>
+__device__ __forceinline__ void cat_store_g(uint8_t* sA, const float2 (&v)[CAT_ITER][8], int kc8, uint32_t sbo,
+                                            int planeA) {
+    const int ntask = TBM * kc8;
+#pragma unroll
+    for (int u = 0; u < CAT_ITER; ++u) {
+        const int task = threadIdx.x + u * CAT_THREADS, i = task / kc8, kc = task % kc8;
+        if (task >= ntask) break;
+        uint32_t w[2 * T][4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+            uint32_t r0[3], i0[3], r1[3], i1[3];
+            split_bits<T>(v[u][e].x, r0); split_bits<T>(v[u][e].y, i0);
+            split_bits<T>(v[u][e + 1].x, r1); split_bits<T>(v[u][e + 1].y, i1);
+#pragma unroll
+            for (int q = 0; q < T; ++q) {
+                w[q][e / 2] = pack_hi(r0[q], r1[q]);
+                w[T + q][e / 2] = pack_hi(i0[q], i1[q]);
+            }
+        }
+        const int off = canon_off(i, kc, sbo);
+#pragma unroll
+        for (int q = 0; q < 2 * T; ++q)
+            *reinterpret_cast<uint4*>(sA + q * planeA + off) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+    }
+}
+
+// DG1b A: rows p0 .. p0 + 127 of the P'' planes, 16-byte chunks by cp.async (zero past the
+// item's rows and past the planes' leading dimension, whose padding columns are zero)
+template <int T>
+__device__ __forceinline__ void cat_load_planes(uint8_t* sA, const CatItem& it, int p0, int kc8, uint32_t sbo,
+                                                int planeA) {
+    const int ntask = TBM * kc8;
+    for (int task = threadIdx.x; task < 2 * T * ntask; task += CAT_THREADS) {
+        const int q = task / ntask, rem = task % ntask, i = rem / kc8, kc = rem % kc8, m = p0 + i;
+        uint8_t* dst = sA + q * planeA + canon_off(i, kc, sbo);
+        const bool ok = m < it.M && kc * 8 < it.a_ld;
+        const bf16* src = ok ? it.a + q * it.a_ps + (int64_t)m * it.a_ld + kc * 8 : it.a;
+        cp16(dst, src, ok ? 16 : 0);
+    }
+    asm volatile("cp.async.commit_group;");
+}
+
+// B: row n of slot j, depth k, from the factor (zero past its rank and K)
+template <int T>
+__device__ __forceinline__ void cat_build_b(uint8_t* sBp, uint8_t* sBn, const CatItem& it, int K, int kc8,
+                                            uint32_t sbo) {
+    const int n8 = (it.rank + 7) & ~7;
+    for (int task = threadIdx.x; task < n8 * kc8; task += CAT_THREADS) {
+        const int n = task / kc8, kc = task % kc8;
+        uint32_t wr[T][4], wi[T][4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+            float2 u0 = make_float2(0.f, 0.f), u1 = u0;
+            const int k = kc * 8 + e;
+            if (n < it.rank && k < K) u0 = __ldg(it.fac + k + (int64_t)K * n);
+            if (n < it.rank && k + 1 < K) u1 = __ldg(it.fac + k + 1 + (int64_t)K * n);
+            uint32_t r0[3], i0[3], r1[3], i1[3];
+            split_bits<T>(u0.x, r0); split_bits<T>(u0.y, i0);
+            split_bits<T>(u1.x, r1); split_bits<T>(u1.y, i1);
+#pragma unroll
+            for (int q = 0; q < T; ++q) {
+                wr[q][e / 2] = pack_hi(r0[q], r1[q]);
+                wi[q][e / 2] = pack_hi(i0[q], i1[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < T; ++q) {
+            const uint4 re = make_uint4(wr[q][0], wr[q][1], wr[q][2], wr[q][3]);
+            const uint4 im = make_uint4(wi[q][0], wi[q][1], wi[q][2], wi[q][3]);
+            // the split is odd in its argument: the terms of -Im are the terms of Im, negated
+            const uint4 nim = make_uint4(im.x ^ 0x80008000u, im.y ^ 0x80008000u, im.z ^ 0x80008000u,
+                                         im.w ^ 0x80008000u);
+            *reinterpret_cast<uint4*>(sBp + canon_off((2 * q) * n8 + n, kc, sbo)) = re;
+            *reinterpret_cast<uint4*>(sBp + canon_off((2 * q + 1) * n8 + n, kc, sbo)) = im;
+            *reinterpret_cast<uint4*>(sBn + canon_off((2 * q) * n8 + n, kc, sbo)) = nim;
+            *reinterpret_cast<uint4*>(sBn + canon_off((2 * q + 1) * n8 + n, kc, sbo)) = re;
+        }
+    }
+}
+
+// the 2T MMAs per K step of the stacked product into the accumulator at TMEM column d0
+// (one thread)
+template <int T>
+__device__ __forceinline__ void cat_issue(uint32_t d0, const uint8_t* sA, const uint8_t* sBp, const uint8_t* sBn,
+                                          int n8, int K16, uint32_t sbo, int planeA) {
+    const uint64_t da = make_desc_sbo(smem_u32(sA), sbo), dbp = make_desc_sbo(smem_u32(sBp), sbo),
+                   dbn = make_desc_sbo(smem_u32(sBn), sbo);
+    for (int ks = 0; ks < K16 / 16; ++ks)
+#pragma unroll
+        for (int p = 0; p < T; ++p) {
+            const uint32_t idesc = idesc_bf16(2 * (T - p) * n8);
+            const uint64_t ar = da + (uint32_t)(p * planeA + ks * 256) / 16;
+            const uint64_t ai = da + (uint32_t)((T + p) * planeA + ks * 256) / 16;
+            const uint32_t d = d0 + (uint32_t)(2 * p * n8);
+            mma_bf16(d, ar, dbp + (uint32_t)(ks * 256) / 16, idesc, (ks > 0 || p > 0) ? 1u : 0u);
+            mma_bf16(d, ai, dbn + (uint32_t)(ks * 256) / 16, idesc, 1u);
+        }
+}
+
+// (L_2 + L_1) + L_0 of the accumulator at TMEM column d0 -> the output planes: warps w
+// and w + 4 read lane quarter w & 3, alternate blocks of 8 columns each.  Output element
+// (m, column n): DG1a row n + r_t r, column i_phi of P''; DG1b row r, column a + r_t n of H.
+template <int T, int MODE>
+__device__ __forceinline__ void cat_epilogue(uint32_t d0, const CatItem& it, int p0, int n_phi) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, n8 = (it.rank + 7) & ~7;
+    const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+    const int m = p0 + (warp & 3) * 32 + lane;
+    const bool row_ok = m < it.M;
+    int64_t base = 0, step = 0;
+    if (row_ok) {
+        if (MODE == CAT_DG1A) {
+            base = (int64_t)it.rt * (m / n_phi) * it.o_ld + m % n_phi;
+            step = it.o_ld;
+        } else {
+            base = (int64_t)(m / it.rt) * it.o_ld + m % it.rt;
+            step = it.rt;
+        }
+    }
+    for (int c0 = (warp >> 2) * 8; c0 < n8; c0 += 16) {
+        uint32_t vr[T][8], vi[T][8];
+#pragma unroll
+        for (int q = 0; q < T; ++q) {
+            tmem_ld8(vr[q], d0 + lanes + (uint32_t)(2 * q * n8 + c0));
+            tmem_ld8(vi[q], d0 + lanes + (uint32_t)(2 * q * n8 + n8 + c0));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        if (!row_ok) continue;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int n = c0 + e;
+            if (n >= it.rank) break;
+            float re = __uint_as_float(vr[T - 1][e]), im = __uint_as_float(vi[T - 1][e]);
+#pragma unroll
+            for (int q = T - 2; q >= 0; --q) {
+                re += __uint_as_float(vr[q][e]);
+                im += __uint_as_float(vi[q][e]);
+            }
+            store_planes<T>(it.out, it.o_ps, base + step * n, make_float2(re, im));
+        }
+    }
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, int tcols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(tcols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+
+// One 128-row tile per CTA.
+template <int T, int MODE>
+__global__ void __launch_bounds__(CAT_THREADS) tc_cat_kernel(const TcCtx c, const CatItem* __restrict__ items,
+                                                            const D1Tile* __restrict__ tiles, int K, int K16,
+                                                            int n8max, int tcols, int n_phi) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const D1Tile t = tiles[blockIdx.x];
+    const CatItem it = items[t.item];
+    const int kc8 = K16 / 8;
+    const uint32_t sbo = (uint32_t)K16 * 16;            // bytes from one 8-row group to the next
+    const int planeA = TBM / 8 * (int)sbo;              // one term plane of A (128 rows)
+    const int bbuf = 2 * T * n8max / 8 * (int)sbo;      // Bpos or Bneg
+    uint8_t* sA = smem;
+    uint8_t* sBp = smem + 2 * T * planeA;
+    uint8_t* sBn = sBp + bbuf;
+    if (warp == 0) tmem_alloc(&tmem_base, tcols);
+    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    if constexpr (MODE == CAT_DG1A) {
+        float2 v[CAT_ITER][8];
+        cat_load_g(v, c, it, t.p0, kc8, n_phi);
+        cat_store_g<T>(sA, v, kc8, sbo, planeA);
+    } else {
+        cat_load_planes<T>(sA, it, t.p0, kc8, sbo, planeA);
+    }
+    cat_build_b<T>(sBp, sBn, it, K, kc8, sbo);
+    if constexpr (MODE == CAT_DG1B) asm volatile("cp.async.wait_group 0;");
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tm = tmem_base;
+    if (tid == 0) {
+        cat_issue<T>(tm, sA, sBp, sBn, (it.rank + 7) & ~7, K16, sbo, planeA);
+        mma_commit(&mbar);
+    }
+    bool ok = mbar_wait(&mbar, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    ok = __syncthreads_and(ok);
+    if (ok) {
+        cat_epilogue<T, MODE>(tm, it, t.p0, n_phi);
+    } else {
+        mbar_wait(&mbar, 0);  // no MMA may still run when TMEM is freed
+        if (tid == 0) atomicAdd(c.err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(tcols));
+}
+
 // ------------------------------------------------------------ operand prep
 // Split planes of an FP32 complex matrix: dst[p][r][k] for r < rows, k < cols,
 // src element (r, k) at src[r * sr + k * sk]; entries k in [cols, ld) stay as they are.
@@ -1316,6 +1576,64 @@ void launch_dg1a(const Plan& P, const TcPlan& M, const TcCtx& c, cudaStream_t s)
     TFMM_CUDA_CHECK(cudaGetLastError());
 }
 
+// The stacked-term form of DG1a (MODE CAT_DG1A) or DG1b (CAT_DG1B) when the stacked N
+// (2 T r8(rank)) fits one MMA and both operands fit shared memory; TFMM_TC_CAT=0 keeps
+// the other forms (for comparisons), as does a DG1a pair count set by the tuning.
+template <class VOff, class MOff>
+void plan_cat(const Plan& P, TcPlan& M, int mode, bf16* Vb, VOff voff, bf16* Mb, MOff moff) {
+    CatPlan& C = mode == CAT_DG1A ? M.cat1a : M.cat1b;
+    C.on = false;
+    if (const char* e = std::getenv("TFMM_TC_CAT"); e && e[0] == '0') return;
+    if (mode == CAT_DG1A && (P.tc_dg1a_pairs != 0 || !fused_enabled())) return;
+    const int T = M.T, R = M.R, nt = P.n_theta, np = P.n_phi;
+    const int K = mode == CAT_DG1A ? nt : np, K16 = (K + 15) & ~15;
+    const int n8max = (int)r8(P.max_rank[mode == CAT_DG1A ? 0 : 1]);
+    if (2 * T * n8max > 256) return;
+    if (mode == CAT_DG1A && TBM * (K16 / 8) > 4 * CAT_THREADS) return;
+    const size_t sbo = (size_t)K16 * 16;
+    const size_t smem = (size_t)2 * T * (TBM / 8) * sbo + (size_t)2 * (2 * T * n8max / 8) * sbo;
+    if (smem > kMaxDynSmem) return;
+    std::vector<CatItem> items(P.items.size());
+    std::vector<D1Tile> tiles;
+    for (size_t q = 0; q < P.items.size(); ++q) {
+        const TuckerItem& d = P.items[q];
+        CatItem& it = items[q];
+        it.g = d.g; it.alpha = d.alpha; it.rt = d.rt;
+        if (mode == CAT_DG1A) {
+            it.fac = P.d_factors + d.uth; it.rank = d.rt; it.M = np * R;
+            it.a = nullptr; it.a_ld = 0; it.a_ps = 0;
+            it.out = Vb + voff((int)q); it.o_ld = r8(np); it.o_ps = (int64_t)d.rt * R * r8(np);
+        } else {
+            it.fac = P.d_factors + d.uphi; it.rank = d.rp; it.M = d.rt * R;
+            it.a = Vb + voff((int)q); it.a_ld = r8(np); it.a_ps = (int64_t)d.rt * R * r8(np);
+            const int64_t ldh = r8((int64_t)d.rt * d.rp);
+            it.out = Mb + moff((int)q); it.o_ld = ldh; it.o_ps = (int64_t)R * ldh;
+        }
+        for (int p0 = 0; p0 < it.M; p0 += TBM) tiles.push_back(D1Tile{(int)q, p0});
+    }
+    TFMM_CUDA_CHECK(device_malloc(&C.items.p, sizeof(CatItem) * items.size()));
+    TFMM_CUDA_CHECK(device_malloc(&C.tiles.p, sizeof(D1Tile) * tiles.size()));
+    TFMM_CUDA_CHECK(cudaMemcpy(C.items.p, items.data(), sizeof(CatItem) * items.size(), cudaMemcpyHostToDevice));
+    TFMM_CUDA_CHECK(cudaMemcpy(C.tiles.p, tiles.data(), sizeof(D1Tile) * tiles.size(), cudaMemcpyHostToDevice));
+    C.ntiles = (int)tiles.size();
+    C.K = K;
+    C.K16 = K16;
+    C.n8max = n8max;
+    C.smem = smem;
+    C.tcols = 32;
+    while (C.tcols < 2 * T * n8max) C.tcols *= 2;
+    C.on = true;
+}
+
+template <int T, int MODE>
+void launch_cat(const Plan& P, const CatPlan& C, const TcCtx& c, cudaStream_t s) {
+    allow_dyn_smem(reinterpret_cast<const void*>(tc_cat_kernel<T, MODE>), kMaxDynSmem);
+    tc_cat_kernel<T, MODE><<<C.ntiles, CAT_THREADS, C.smem, s>>>(c, static_cast<const CatItem*>(C.items.p),
+                                                               static_cast<const D1Tile*>(C.tiles.p), C.K, C.K16,
+                                                               C.n8max, C.tcols, P.n_phi);
+    TFMM_CUDA_CHECK(cudaGetLastError());
+}
+
 }  // namespace
 
 TcPlan* get_tc_plan(Plan& P, int R, int T, cudaStream_t s) {
@@ -1446,7 +1764,11 @@ TcPlan* get_tc_plan(Plan& P, int R, int T, cudaStream_t s) {
         M.v_off[q] = of[q].v;
     }
     plan_fused34(P, M, F, tci, Mb, [&](int q) { return M.m_off[q]; });
-    plan_dg1a(P, M, F, tci, Vb, [&](int q) { return M.v_off[q]; });
+    const auto voff = [&](int q) { return M.v_off[q]; };
+    const auto moff = [&](int q) { return M.m_off[q]; };
+    plan_cat(P, M, CAT_DG1A, Vb, voff, Mb, moff);
+    if (!M.cat1a.on) plan_dg1a(P, M, F, tci, Vb, voff);
+    plan_cat(P, M, CAT_DG1B, Vb, voff, Mb, moff);
     P.tc.push_back(std::move(tp));
     return P.tc.back().get();
 }
@@ -1456,7 +1778,8 @@ void tc_replan_shapes(Plan& P) {
     TFMM_CUDA_CHECK(cudaDeviceSynchronize());  // no launch may still read the old lists
     for (auto& mp : P.tc) {
         TcPlan& M = *mp;
-        for (DeviceBuffer* b : {&M.f34_items, &M.f34_tiles, &M.dg1a_items, &M.dg1a_tiles}) {
+        for (DeviceBuffer* b : {&M.f34_items, &M.f34_tiles, &M.dg1a_items, &M.dg1a_tiles, &M.cat1a.items,
+                                &M.cat1a.tiles}) {
             if (b->p) cudaFree(b->p);
             b->p = nullptr;
         }
@@ -1465,7 +1788,11 @@ void tc_replan_shapes(Plan& P) {
         bf16* Mb = reinterpret_cast<bf16*>(M.buf[2]);
         bf16* Vb = reinterpret_cast<bf16*>(M.buf[3]);
         plan_fused34(P, M, F, tci, Mb, [&](int q) { return M.m_off[q]; });
-        plan_dg1a(P, M, F, tci, Vb, [&](int q) { return M.v_off[q]; });
+        const auto voff = [&](int q) { return M.v_off[q]; };
+        const auto moff = [&](int q) { return M.m_off[q]; };
+        plan_cat(P, M, CAT_DG1A, Vb, voff, Mb, moff);
+        M.dg1a = false;
+        if (!M.cat1a.on) plan_dg1a(P, M, F, tci, Vb, voff);
     }
 }
 
@@ -1507,11 +1834,16 @@ void tc_disaggregate_t(Plan& P, TcPlan& M, const float2* spec, int R, int weight
                                             R, P.G, P.n_theta, P.n_phi);
         TFMM_CUDA_CHECK(cudaGetLastError());
     }
-    if (M.dg1a)
+    if (M.cat1a.on)
+        launch_cat<T, CAT_DG1A>(P, M.cat1a, c, s);
+    else if (M.dg1a)
         launch_dg1a<T>(P, M, c, s);
     else
         launch_tc<T, TDG1A>(M.st[TDG1A], c, s);
-    launch_tc<T, TDG1B>(M.st[TDG1B], c, s);
+    if (M.cat1b.on)
+        launch_cat<T, CAT_DG1B>(P, M.cat1b, c, s);
+    else
+        launch_tc<T, TDG1B>(M.st[TDG1B], c, s);
     launch_tc<T, TDG2>(M.st[TDG2], c, s);
     launch_tc<T, TDG3>(M.st[TDG3], c, s);
 }

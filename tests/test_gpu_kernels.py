@@ -312,6 +312,39 @@ def test_tensor_core_chain_matches_oracle(name, R, terms, tol):
     print(f"{name} R={R} terms={terms}: worst aggregation {worst[0]:.2e}, disaggregation {worst[1]:.2e}")
 
 
+@pytest.mark.parametrize("terms", [3, 2])
+def test_stacked_dg1_forms_match_the_generic_stage_kernel(terms, monkeypatch):
+    """DG1a / DG1b with the BF16 terms of U_theta / U_phi stacked along N (the default when
+    they fit) against the generic stage kernels (TFMM_TC_CAT=0 while the chain is planned)
+    and the oracle: both within the chain's tolerance, and within twice it of each other."""
+    tfmm = _tfmm()
+    nt, npf, nbetas, rank_fn = CASES["paper_like"]
+    R = 16
+    n_rwg, members, T, factors = _case(700 + R, nt, npf, nbetas, rank_fn)
+    w = np.random.default_rng(19).uniform(0.05, 1.0, nt * npf)
+    G, nd = len(members), nt * npf
+    g_in = complex_gaussian((R, G, 2, nd), 900 + R)
+    gd = torch.from_numpy(g_in.astype(np.complex64)).cuda()
+    tol = 1e-6 if terms == 3 else 5e-5
+    out = {}
+    for cat in ("1", "0"):
+        monkeypatch.setenv("TFMM_TC_CAT", cat)
+        plan = tfmm.tfmm_plan_from_tucker(n_rwg, nt, npf, members, factors, weights=w, max_rhs=R,
+                                          mrhs_precision=terms)
+        yd = torch.zeros((R, n_rwg), dtype=torch.complex64, device="cuda")
+        tfmm.tfmm_disaggregate(plan, gd, yd)
+        torch.cuda.synchronize()
+        assert plan.info["kernel_errors"] == 0
+        out[cat] = yd.cpu().numpy()
+    monkeypatch.delenv("TFMM_TC_CAT")
+    for r in range(R):
+        refy = apply.disaggregate_all(T, members, g_in[r], n_rwg, w)
+        for ids in members:
+            for cat in ("1", "0"):
+                assert _close(out[cat][r, ids], refy[ids], tol), (cat, r)
+            assert _close(out["1"][r, ids], out["0"][r, ids], 2 * tol), r
+
+
 def test_tensor_core_chain_on_far_field_factors():
     """The 3-term tensor-core chain on the oracle's own T-HOSVD factors of real far-field
     tensors (orthonormal factors, paper-shaped ranks): 10-lambda sphere, 1-lambda boxes,
