@@ -139,6 +139,7 @@ struct TcProb {             // one grouped-GEMM problem D (M x N) = A (M x K) B 
 struct TcStagePlan {
     TcProb* d_probs = nullptr;
     MrTile* d_tiles = nullptr;
+    void* d_maps = nullptr;       // CUtensorMap x 4 per problem (A0, B0, A1, B1) when TMA feeds the stage
     int n_tiles = 0, n_probs = 0;
     int max_kt = 1, max_bn = 16;  // largest K-tile count and BN over the stage's problems
     ~TcStagePlan();

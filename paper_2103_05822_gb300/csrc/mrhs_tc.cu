@@ -36,6 +36,8 @@
 // steps when the shapes allow: tc_ag34_kernel fuses AG3 and AG4 (V'' never leaves the
 // SM), and tc_dg1a_kernel runs DG1a transposed, U_theta^T as A and 128 (i_phi, r)
 // pairs of the spectra as N, so that its MMAs are wide.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -600,6 +602,171 @@ __device__ __forceinline__ uint32_t idesc_bf16(int N) {
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar)));
+}
+
+// ------------------------------------------- stage kernel with a TMA-fed ring
+// The long-K stages (AG1, AG2, DG2, DG3) as tc_gemm_kernel<T, S, true>, the same MMAs in
+// the same order and the same chunked accumulation, but with the operands fed by the
+// tensor-memory accelerator: one thread keeps `nst` K steps of 16 in flight (two 3-D
+// boxes of 8 K x rows x 2T planes per operand and K step, zero-filled past the matrix
+// edges by the copy engine), issues the MMAs of a K step as soon as its bytes have
+// arrived and refills the stage of the previous K step once those MMAs are done; the
+// other threads only take part in the chunk drains and the epilogue.  A box lands in
+// shared memory as [8-element K chunk][plane][row][8 elements], i.e. 8 x 16-byte core
+// matrices with the next 8 rows 128 bytes on and the next K chunk one box on, which is
+// what the MMA descriptors below describe.
+constexpr int NST_TMA_MAX = 8;
+
+__device__ __forceinline__ uint64_t make_desc_lbo(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;   // next core matrix along K
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;   // next 8-row group
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+            "r"(smem_u32(dst)), "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+template <int T, int S>
+__global__ void __launch_bounds__(2 * TTHREADS)
+    tc_gemm_tma_kernel(const TcCtx c, const TcProb* __restrict__ probs, const CUtensorMap* __restrict__ maps,
+                       const MrTile* __restrict__ tiles, int nst, int tcols, int cofs, int chunk) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ __align__(8) uint64_t full[NST_TMA_MAX], empty[NST_TMA_MAX];
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const MrTile t = tiles[blockIdx.x];
+    const TcProb p = probs[t.prob];
+    const CUtensorMap* mp = maps + 4 * (int64_t)t.prob;  // A0, B0, A1, B1
+    const int BN = p.BN;
+    const int abox = 8 * TBM * 2 * T * 2, bbox = 8 * BN * 2 * T * 2;
+    const int stage_bytes = 2 * abox + 2 * bbox;  // one K step of 16
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(tcols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0)
+        for (int s = 0; s < nst; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[s])), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[s])), "r"(1));
+        }
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tm = tmem_base;
+    const int ks0 = (p.K0 + 15) / 16, kt0 = (p.K0 + 31) / 32;
+    const int KS = ks0 + (p.K1 > 0 ? (p.K1 + 15) / 16 : 0);
+    // chunks of `chunk` k-tiles of 32 as in tc_gemm_kernel (a segment's last k-tile may hold
+    // one K step), so that both kernels round alike: k-tile of a K step, and its first / last
+    auto ktile = [&](int ks) { return ks < ks0 ? ks / 2 : kt0 + (ks - ks0) / 2; };
+    auto kt_first = [&](int ks) { return ks < ks0 ? (ks % 2) == 0 : ((ks - ks0) % 2) == 0; };
+    auto kt_last = [&](int ks) { return ks + 1 == KS || ks + 1 == ks0 || ktile(ks + 1) != ktile(ks); };
+    auto produce = [&](int ks) {
+        uint8_t* base = smem + (ks % nst) * stage_bytes;
+        const bool seg1 = ks >= ks0;
+        const int koff = (seg1 ? ks - ks0 : ks) * 16;
+        const CUtensorMap* ma = mp + (seg1 ? 2 : 0);
+        const CUtensorMap* mb = mp + (seg1 ? 3 : 1);
+        uint64_t* bar = &full[ks % nst];
+        mbar_expect_tx(bar, (uint32_t)stage_bytes);
+        tma_load_3d(base, ma, koff, t.m0, 0, bar);
+        tma_load_3d(base + abox, ma, koff + 8, t.m0, 0, bar);
+        tma_load_3d(base + 2 * abox, mb, koff, t.n0, 0, bar);
+        tma_load_3d(base + 2 * abox + bbox, mb, koff + 8, t.n0, 0, bar);
+    };
+    int produced = 0, consumed = 0;
+    if (tid == 0)
+        for (; produced < min(nst, KS); ++produced) produce(produced);
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TBM >> 4) << 24);
+    const uint32_t idesc_neg = idesc | (1u << 13);
+    const uint32_t q_lanes = (uint32_t)((warp & 3) * 32) << 16;
+    const int q_col = (warp >> 2) * 64;
+    float accr[64], acci[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) accr[j] = acci[j] = 0.f;
+    bool ok = true;
+    for (int ks = 0; ks < KS; ++ks) {
+        const int st = ks % nst;
+        const uint32_t ph = (uint32_t)(ks / nst) & 1u;
+        if (tid == 0 && ok) {
+            ok = mbar_wait(&full[st], ph);
+            if (ok) {
+                consumed = ks + 1;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t base = smem_u32(smem + st * stage_bytes);
+                constexpr int PI[6] = {0, 0, 1, 0, 1, 2}, PJ[6] = {0, 1, 0, 2, 1, 0};
+                const bool fresh = (ktile(ks) % chunk) == 0 && kt_first(ks);  // first K step of a chunk
+#pragma unroll
+                for (int q = 0; q < n_products<T>(); ++q) {
+                    const uint64_t ar = make_desc_lbo(base + PI[q] * TBM * 16, abox, 128);
+                    const uint64_t ai = make_desc_lbo(base + (T + PI[q]) * TBM * 16, abox, 128);
+                    const uint64_t br = make_desc_lbo(base + 2 * abox + PJ[q] * BN * 16, bbox, 128);
+                    const uint64_t bi = make_desc_lbo(base + 2 * abox + (T + PJ[q]) * BN * 16, bbox, 128);
+                    // the leading product (hi x hi) restarts its accumulator every chunk; the
+                    // correction products accumulate apart over the whole K (columns 2 cofs on)
+                    const bool lo = q > 0;
+                    const uint32_t acc = lo ? ((ks > 0 || q > 1) ? 1u : 0u) : (fresh ? 0u : 1u);
+                    const uint32_t d = tm + (lo ? 2 * cofs : 0);
+                    mma_bf16(d, ar, br, idesc, acc);
+                    mma_bf16(d, ai, bi, idesc_neg, 1u);
+                    mma_bf16(d + cofs, ar, bi, idesc, acc);
+                    mma_bf16(d + cofs, ai, br, idesc, 1u);
+                }
+                mma_commit(&empty[st]);
+                // refill the stage of K step ks - 1 once its MMAs are done (those of ks keep
+                // the tensor pipe busy meanwhile)
+                if (ks >= 1 && produced < KS) {
+                    ok = mbar_wait(&empty[(ks - 1) % nst], (uint32_t)((ks - 1) / nst) & 1u);
+                    if (ok) produce(produced++);
+                }
+            }
+        }
+        if (kt_last(ks) && (ktile(ks) % chunk) == chunk - 1 && ks + 1 < KS) {
+            // end of a chunk: once its MMAs are done, add the leading-product accumulator
+            // into the registers; the next K step restarts it
+            ok = mbar_wait(&empty[st], ph) && ok;
+            ok = __syncthreads_and(ok);
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (ok) drain_add(accr, acci, tm + q_lanes, cofs, q_col, BN);
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
+        }
+    }
+    // always wait (bounded) for the last commit: no MMA may still read TMEM when it is freed
+    if (KS > 0 && !mbar_wait(&empty[(KS - 1) % nst], (uint32_t)((KS - 1) / nst) & 1u)) ok = false;
+    if (tid == 0)  // copies still in flight after a wait gave up land before the CTA exits
+        for (int ks = consumed; ks < produced; ++ks) mbar_wait(&full[ks % nst], (uint32_t)(ks / nst) & 1u);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    ok = __syncthreads_and(ok);
+    if (!ok) {
+        if (tid == 0) atomicAdd(c.err, 1);
+    } else {
+        drain_add(accr, acci, tm + q_lanes, cofs, q_col, BN);
+        drain_add(accr, acci, tm + q_lanes + 2 * cofs, cofs, q_col, BN);
+        const int row = t.m0 + (warp & 3) * 32 + lane;
+        if (row < p.M) {
+#pragma unroll
+            for (int jj = 0; jj < 64; ++jj) {
+                const int cc = q_col + jj, col = t.n0 + cc;
+                if (cc < BN && col < p.N) epilogue<T, S>(c, p, row, col, make_float2(accr[jj], acci[jj]));
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(tcols));
 }
 
 constexpr int F34_WORKERS = 512;               // 16 warps, four per TMEM lane quarter
@@ -1312,6 +1479,17 @@ void launch_tc(const TcStagePlan& st, const TcCtx& c, cudaStream_t s) {
     if (kSmemSM / (smem + 2048) > (size_t)ctas_tmem) smem = std::min(kMaxDyn, kSmemSM / ctas_tmem - 2048);
     const int chunk = tc_chunk_ktiles();
     const TcProb* probs = reinterpret_cast<const TcProb*>(st.d_probs);
+    if (st.d_maps && hsplit) {
+        // TMA-fed ring of K steps of 16: as many stages as fit next to nothing else
+        const size_t stage = (size_t)2 * 8 * 2 * T * 2 * (TBM + st.max_bn);
+        const int nst_tma = (int)std::min<size_t>(NST_TMA_MAX, kMaxDyn / stage);
+        allow_dyn_smem(reinterpret_cast<const void*>(tc_gemm_tma_kernel<T, S>), kMaxDyn);
+        tc_gemm_tma_kernel<T, S><<<st.n_tiles, 2 * TTHREADS, nst_tma * stage, s>>>(
+            c, probs, static_cast<const CUtensorMap*>(st.d_maps), st.d_tiles, nst_tma, tcols, cofs,
+            chunk > 0 ? chunk : 1 << 30);
+        TFMM_CUDA_CHECK(cudaGetLastError());
+        return;
+    }
     if constexpr (S == TAG1 || S == TAG2 || S == TDG1B || S == TDG2 || S == TDG3) {
         if (hsplit && chunk > 0 && st.max_kt > chunk) {
             allow_dyn_smem(reinterpret_cast<const void*>(tc_gemm_kernel<T, S, true>), kMaxDyn);
@@ -1331,6 +1509,7 @@ void launch_tc(const TcStagePlan& st, const TcCtx& c, cudaStream_t s) {
 TcStagePlan::~TcStagePlan() {
     if (d_probs) cudaFree(d_probs);
     if (d_tiles) cudaFree(d_tiles);
+    if (d_maps) cudaFree(d_maps);
 }
 
 TcPlan::~TcPlan() {
@@ -1408,6 +1587,61 @@ void add_tc_tiles(std::vector<MrTile>& tiles, int prob, int M, int N) {
 }
 
 int bn_of(int N) { return (int)std::min<int64_t>(TBN_MAX, (N + 15) / 16 * 16); }
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }();
+    return fn;
+}
+
+// 3-D map of the 2T planes of a K-major matrix (K x rows x planes, boxes of 8 K x
+// box_rows x 2T); false when the layout breaks a rule of the copy engine.
+bool encode_planes(CUtensorMap* m, const bf16* base, int64_t K, int64_t rows, int64_t ld, int64_t ps, int T,
+                   int box_rows) {
+    const auto fn = tensor_map_encoder();
+    if (!fn || !base || K < 1 || rows < 1 || ld < K || ld % 8 || ps % 8 || ps < rows * ld ||
+        reinterpret_cast<uintptr_t>(base) % 16)
+        return false;
+    cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)(2 * T)};
+    cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)ps * 2};
+    cuuint32_t box[3] = {8, (cuuint32_t)box_rows, (cuuint32_t)(2 * T)};
+    cuuint32_t es[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16*>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Tensor maps (A0, B0, A1, B1) of every problem of a stage for tc_gemm_tma_kernel; the
+// stage keeps the cp.async kernel when one cannot be made or TFMM_TC_TMA=0.
+void build_stage_maps(TcStagePlan& st, const std::vector<TcProb>& probs, int T) {
+    if (const char* e = std::getenv("TFMM_TC_TMA"); e && e[0] == '0') return;
+    if (probs.empty()) return;
+    std::vector<CUtensorMap> maps(4 * probs.size());
+    for (size_t i = 0; i < probs.size(); ++i) {
+        const TcProb& p = probs[i];
+        CUtensorMap* m = &maps[4 * i];
+        bool ok = encode_planes(m + 0, p.A0, p.K0, p.M, p.a_ld0, p.a_ps0, T, TBM) &&
+                  encode_planes(m + 1, p.B0, p.K0, p.N, p.b_ld0, p.b_ps0, T, p.BN);
+        if (ok && p.K1 > 0)
+            ok = encode_planes(m + 2, p.A1, p.K1, p.M, p.a_ld1, p.a_ps1, T, TBM) &&
+                 encode_planes(m + 3, p.B1, p.K1, p.N, p.b_ld1, p.b_ps1, T, p.BN);
+        else {
+            m[2] = m[0];
+            m[3] = m[1];
+        }
+        if (!ok) return;
+    }
+    TFMM_CUDA_CHECK(device_malloc(&st.d_maps, sizeof(CUtensorMap) * maps.size()));
+    TFMM_CUDA_CHECK(cudaMemcpy(st.d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice));
+}
 
 void upload_tc_stage(TcStagePlan& st, const std::vector<TcProb>& probs, const std::vector<MrTile>& tiles) {
     st.n_tiles = (int)tiles.size();
@@ -1756,6 +1990,7 @@ TcPlan* get_tc_plan(Plan& P, int R, int T, cudaStream_t s) {
     }
     for (int st = 0; st < 8; ++st) {
         upload_tc_stage(M.st[st], pr[st], tl[st]);
+        if (st == TAG1 || st == TAG2 || st == TDG2 || st == TDG3) build_stage_maps(M.st[st], pr[st], T);
     }
     M.m_off.resize(nI);
     M.v_off.resize(nI);

@@ -345,6 +345,35 @@ def test_stacked_dg1_forms_match_the_generic_stage_kernel(terms, monkeypatch):
             assert _close(out["1"][r, ids], out["0"][r, ids], 2 * tol), r
 
 
+@pytest.mark.parametrize("terms", [3, 2])
+@pytest.mark.parametrize("name,R", [("paper_like", 16), ("ragged", 7)])
+def test_tma_fed_stages_equal_the_cp_async_kernel(name, R, terms, monkeypatch):
+    """AG1, AG2, DG2 and DG3 fed by the tensor-memory accelerator (the default) against
+    the same stages with operands staged by cp.async (TFMM_TC_TMA=0 while the chain is
+    planned): the same MMAs in the same order, so the same bits."""
+    tfmm = _tfmm()
+    nt, npf, nbetas, rank_fn = CASES[name]
+    n_rwg, members, T, factors = _case(700 + R, nt, npf, nbetas, rank_fn)
+    w = np.random.default_rng(19).uniform(0.05, 1.0, nt * npf)
+    G, nd = len(members), nt * npf
+    X = torch.from_numpy(complex_gaussian((R, n_rwg), 800 + R).astype(np.complex64)).cuda()
+    g_in = torch.from_numpy(complex_gaussian((R, G, 2, nd), 900 + R).astype(np.complex64)).cuda()
+    out = {}
+    for tma in ("1", "0"):
+        monkeypatch.setenv("TFMM_TC_TMA", tma)
+        plan = tfmm.tfmm_plan_from_tucker(n_rwg, nt, npf, members, factors, weights=w, max_rhs=R,
+                                          mrhs_precision=terms)
+        spec = torch.empty((R, G, 2, nd), dtype=torch.complex64, device="cuda")
+        tfmm.tfmm_aggregate(plan, X, spec)
+        y = torch.zeros((R, n_rwg), dtype=torch.complex64, device="cuda")
+        tfmm.tfmm_disaggregate(plan, g_in, y)
+        torch.cuda.synchronize()
+        assert plan.info["kernel_errors"] == 0
+        out[tma] = (spec, y)
+    monkeypatch.delenv("TFMM_TC_TMA")
+    assert torch.equal(out["1"][0], out["0"][0]) and torch.equal(out["1"][1], out["0"][1])
+
+
 def test_tensor_core_chain_on_far_field_factors():
     """The 3-term tensor-core chain on the oracle's own T-HOSVD factors of real far-field
     tensors (orthonormal factors, paper-shaped ranks): 10-lambda sphere, 1-lambda boxes,
