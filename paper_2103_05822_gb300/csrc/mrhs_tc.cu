@@ -26,6 +26,7 @@
 // Steps (per group g and component alpha; see mrhs.cu for the FP32 version):
 //   AG1  T^T (r_b x R)            = U_beta^T . X_g          A: U_beta^T [c][n]   B: X_g   [r][n]
 //   AG2  M   (m x R)              = C_(3)^T  . T            A: C_(3)^T  [ab][c]  B: T     [r][c]
+//        (the rows of C_(3)^T in the order b + r_p a, so that M' leaves in runs of b)
 //   AG3  V'  (r_t R x n_phi)      = M'       . U_phi^T      A: M'  [a+r_t r][b]  B: U_phi [i_phi][b]
 //   AG4  F'  (n_phi R x n_theta)  = V''      . U_theta^T    A: V'' [i_phi+n_phi r][a]  B: U_theta [i_theta][a]
 //   DG1a P'  (n_phi R x r_t)      = G'       . U_theta      A: G'  [i_phi+n_phi r][i_theta]  B: U_theta^T [a][i_theta]
@@ -263,8 +264,8 @@ __device__ __forceinline__ void epilogue(const TcCtx& c, const TcProb& p, int i,
         case TAG1:  // T stored [r][c]: row j (= r), column i (= c)
             store_planes<T>(o, p.o_ps, (int64_t)j * p.o_ld + i, v);
             break;
-        case TAG2: {  // M' stored [a + r_t r][b]; i = a + r_t b, j = r
-            const int a = i % p.rt, b = i / p.rt;
+        case TAG2: {  // M' stored [a + r_t r][b]; i = b + r_p a (the order of the C_(3)^T planes), j = r
+            const int rp = p.M / p.rt, a = i / rp, b = i % rp;
             store_planes<T>(o, p.o_ps, (int64_t)(a + p.rt * j) * p.o_ld + b, v);
         } break;
         case TAG3: {  // V'' stored [i_phi + n_phi r][a]; i = a + r_t r, j = i_phi
@@ -1341,15 +1342,17 @@ __global__ void __launch_bounds__(CAT_THREADS) tc_cat_kernel(const TcCtx c, cons
     if (warp == 0) tmem_alloc(&tmem_base, tcols);
     if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;");
+    // A's loads first, B built while they are in flight
     if constexpr (MODE == CAT_DG1A) {
         float2 v[CAT_ITER][8];
         cat_load_g(v, c, it, t.p0, kc8, n_phi);
+        cat_build_b<T>(sBp, sBn, it, K, kc8, sbo);
         cat_store_g<T>(sA, v, kc8, sbo, planeA);
     } else {
         cat_load_planes<T>(sA, it, t.p0, kc8, sbo, planeA);
+        cat_build_b<T>(sBp, sBn, it, K, kc8, sbo);
+        asm volatile("cp.async.wait_group 0;");
     }
-    cat_build_b<T>(sBp, sBn, it, K, kc8, sbo);
-    if constexpr (MODE == CAT_DG1B) asm volatile("cp.async.wait_group 0;");
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -1376,13 +1379,16 @@ __global__ void __launch_bounds__(CAT_THREADS) tc_cat_kernel(const TcCtx c, cons
 // ------------------------------------------------------------ operand prep
 // Split planes of an FP32 complex matrix: dst[p][r][k] for r < rows, k < cols,
 // src element (r, k) at src[r * sr + k * sk]; entries k in [cols, ld) stay as they are.
+// inner > 0: row r of the planes is source row (r / inner) + outer (r % inner) (the rows
+// of C_(3)^T, index a + r_t b, taken in the order b + r_p a).
 template <int T>
 __global__ void planes_kernel(const float2* __restrict__ src, int rows, int cols, int64_t sr, int64_t sk,
-                              bf16* __restrict__ dst, int64_t ld, int64_t ps) {
+                              bf16* __restrict__ dst, int64_t ld, int64_t ps, int inner, int outer) {
     const int64_t total = (int64_t)rows * cols;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(e / cols), k = (int)(e % cols);
-        store_planes<T>(dst, ps, (int64_t)r * ld + k, src[(int64_t)r * sr + (int64_t)k * sk]);
+        const int rs = inner > 0 ? r / inner + outer * (r % inner) : r;
+        store_planes<T>(dst, ps, (int64_t)r * ld + k, src[(int64_t)rs * sr + (int64_t)k * sk]);
     }
 }
 
@@ -1537,7 +1543,7 @@ void build_tc_factors(Plan& P, int T, cudaStream_t s) {
         const int m = d.rt * d.rp;
         add(t.ubT, d.rb, d.n_beta);   // [c][n]
         add(t.ub, d.n_beta, d.rb);    // [n][c]
-        add(t.c3T, m, d.rb);          // [ab][c]
+        add(t.c3T, m, d.rb);          // [ab][c], rows in the order b + r_p a
         add(t.c3, d.rb, m);           // [c][ab]
         add(t.uphT, np, d.rp);        // [i_phi][b]
         add(t.uph, d.rp, np);         // [b][i_phi]
@@ -1547,12 +1553,15 @@ void build_tc_factors(Plan& P, int T, cudaStream_t s) {
     TFMM_CUDA_CHECK(device_malloc(&P.tc_fac[T].p, sizeof(bf16) * std::max<int64_t>(off, 1)));
     TFMM_CUDA_CHECK(cudaMemsetAsync(P.tc_fac[T].p, 0, sizeof(bf16) * std::max<int64_t>(off, 1), s));
     bf16* base = reinterpret_cast<bf16*>(P.tc_fac[T].p);
-    auto conv = [&](const float2* src, int rows, int cols, int64_t sr, int64_t sk, const TcMat& m) {
+    auto conv = [&](const float2* src, int rows, int cols, int64_t sr, int64_t sk, const TcMat& m, int inner = 0,
+                    int outer = 0) {
         const int64_t ps = (int64_t)m.rows * m.ld;
         if (T == 2)
-            planes_kernel<2><<<g1d((int64_t)rows * cols), 256, 0, s>>>(src, rows, cols, sr, sk, base + m.off, m.ld, ps);
+            planes_kernel<2><<<g1d((int64_t)rows * cols), 256, 0, s>>>(src, rows, cols, sr, sk, base + m.off, m.ld, ps,
+                                                                       inner, outer);
         else
-            planes_kernel<3><<<g1d((int64_t)rows * cols), 256, 0, s>>>(src, rows, cols, sr, sk, base + m.off, m.ld, ps);
+            planes_kernel<3><<<g1d((int64_t)rows * cols), 256, 0, s>>>(src, rows, cols, sr, sk, base + m.off, m.ld, ps,
+                                                                       inner, outer);
     };
     for (size_t q = 0; q < P.items.size(); ++q) {
         const TuckerItem& d = P.items[q];
@@ -1564,7 +1573,7 @@ void build_tc_factors(Plan& P, int T, cudaStream_t s) {
         const float2* ut = P.d_factors + d.uth;     // U_theta:       (i_theta, a) at i_theta + n_theta a
         conv(ub, d.rb, d.n_beta, d.ld_nb, 1, t.ubT);
         conv(ub, d.n_beta, d.rb, 1, d.ld_nb, t.ub);
-        conv(cc, m, d.rb, 1, d.ld_ab, t.c3T);
+        conv(cc, m, d.rb, 1, d.ld_ab, t.c3T, d.rp, d.rt);  // rows b + r_p a: AG2 writes M' in runs of b
         conv(cc, d.rb, m, d.ld_ab, 1, t.c3);
         conv(up, np, d.rp, 1, np, t.uphT);
         conv(up, d.rp, np, np, 1, t.uph);
