@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(CH ? 2 * TTHREADS : TTHREADS)
     // always wait (bounded) for the last commit: no MMA may still read TMEM when it is freed
     if (KT > 0 && !mbar_wait(&mbar[(KT - 1) % NST], ((KT - 1) / NST) & 1)) ok = false;
     asm volatile("tcgen05.fence::after_thread_sync;");
-    // one verdict for the whole CTA: the TMEM loads below are warp-collective
+    // one outcome for the whole CTA: the TMEM loads below are warp-collective
     ok = __syncthreads_and(ok);
     if (!ok) {
         if (tid == 0) atomicAdd(c.err, 1);
