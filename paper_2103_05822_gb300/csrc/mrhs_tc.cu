@@ -155,6 +155,27 @@ __device__ __forceinline__ void split_terms(float v, bf16* t) {
     for (int q = 0; q < T; ++q) t[q] = __ushort_as_bfloat16((unsigned short)(b[q] >> 16));
 }
 
+// Two values split at once, one word per term (x0 in the low half, x1 in the high half):
+// the hardware conversion rounds both to bfloat16 (to nearest, ties to even), the
+// remainders are exact in FP32, and the same again; with T = 3 the last remainder has at
+// most 8 significant bits, so the three terms hold each value exactly, as with
+// split_bits.  Rounding to nearest is odd in its argument: the terms of -x are the terms
+// of x, negated.  Half the instructions of two split_bits calls and the packing.
+template <int T>
+__device__ __forceinline__ void split_pack(float x0, float x1, uint32_t (&w)[3]) {
+    uint32_t h;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(x1), "f"(x0));
+    w[0] = h;
+    const float r0 = x0 - __uint_as_float(h << 16), r1 = x1 - __uint_as_float(h & 0xffff0000u);
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(r1), "f"(r0));
+    w[1] = h;
+    if (T == 3) {
+        const float s0 = r0 - __uint_as_float(h << 16), s1 = r1 - __uint_as_float(h & 0xffff0000u);
+        asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(s1), "f"(s0));
+        w[2] = h;
+    }
+}
+
 // two split values -> one word per term plane (lower index in the low half)
 __device__ __forceinline__ uint32_t pack_hi(uint32_t lo_word, uint32_t hi_word) {
     return __byte_perm(lo_word, hi_word, 0x7632);
@@ -205,13 +226,13 @@ __device__ __forceinline__ void load_g_tile(uint8_t* st, const TcCtx& c, const T
         uint32_t w[2 * T][4];
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
-            uint32_t r0[3], i0[3], r1[3], i1[3];
-            split_bits<T>(v[i][e].x, r0); split_bits<T>(v[i][e].y, i0);
-            split_bits<T>(v[i][e + 1].x, r1); split_bits<T>(v[i][e + 1].y, i1);
+            uint32_t pr[3], pi[3];
+            split_pack<T>(v[i][e].x, v[i][e + 1].x, pr);
+            split_pack<T>(v[i][e].y, v[i][e + 1].y, pi);
 #pragma unroll
             for (int q = 0; q < T; ++q) {
-                w[q][e / 2] = pack_hi(r0[q], r1[q]);
-                w[T + q][e / 2] = pack_hi(i0[q], i1[q]);
+                w[q][e / 2] = pr[q];
+                w[T + q][e / 2] = pi[q];
             }
         }
         const int off = (r >> 3) * 512 + kc * 128 + (r & 7) * 16;
@@ -891,16 +912,14 @@ __global__ void __launch_bounds__(F34_THREADS) tc_ag34_kernel(const TcCtx c, con
                         asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
                         for (int e = 0; e < 8; e += 2) {
-                            uint32_t tr0[3], ti0[3], tr1[3], ti1[3];
+                            uint32_t pr[3], pi[3];
                             const int k = kc * 8 + e;
-                            split_bits<T>(k < it.rt ? __uint_as_float(vr[e]) : 0.f, tr0);
-                            split_bits<T>(k < it.rt ? __uint_as_float(vi[e]) : 0.f, ti0);
-                            split_bits<T>(k + 1 < it.rt ? __uint_as_float(vr[e + 1]) : 0.f, tr1);
-                            split_bits<T>(k + 1 < it.rt ? __uint_as_float(vi[e + 1]) : 0.f, ti1);
+                            split_pack<T>(k < it.rt ? __uint_as_float(vr[e]) : 0.f, k + 1 < it.rt ? __uint_as_float(vr[e + 1]) : 0.f, pr);
+                            split_pack<T>(k < it.rt ? __uint_as_float(vi[e]) : 0.f, k + 1 < it.rt ? __uint_as_float(vi[e + 1]) : 0.f, pi);
 #pragma unroll
                             for (int q = 0; q < T; ++q) {
-                                w[q][e / 2] = pack_hi(tr0[q], tr1[q]);
-                                w[T + q][e / 2] = pack_hi(ti0[q], ti1[q]);
+                                w[q][e / 2] = pr[q];
+                                w[T + q][e / 2] = pi[q];
                             }
                         }
 #pragma unroll
@@ -1029,13 +1048,13 @@ __global__ void __launch_bounds__(D1_THREADS) tc_dg1a_kernel(const TcCtx c, cons
         uint32_t w[2 * T][4];
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
-            uint32_t r0[3], i0[3], r1[3], i1[3];
-            split_bits<T>(v[u][e].x, r0); split_bits<T>(v[u][e].y, i0);
-            split_bits<T>(v[u][e + 1].x, r1); split_bits<T>(v[u][e + 1].y, i1);
+            uint32_t pr[3], pi[3];
+            split_pack<T>(v[u][e].x, v[u][e + 1].x, pr);
+            split_pack<T>(v[u][e].y, v[u][e + 1].y, pi);
 #pragma unroll
             for (int q = 0; q < T; ++q) {
-                w[q][e / 2] = pack_hi(r0[q], r1[q]);
-                w[T + q][e / 2] = pack_hi(i0[q], i1[q]);
+                w[q][e / 2] = pr[q];
+                w[T + q][e / 2] = pi[q];
             }
         }
         const int off = (i >> 3) * (K * 16) + kc * 128 + (i & 7) * 16;
@@ -1085,13 +1104,13 @@ __global__ void __launch_bounds__(D1_THREADS) tc_dg1a_kernel(const TcCtx c, cons
 #pragma unroll
                 for (int e = 0; e < 8; e += 2) {
                     const float2 x0 = stage[a * NP + c8 + e], x1 = stage[a * NP + c8 + e + 1];
-                    uint32_t r0[3], i0[3], r1[3], i1[3];
-                    split_bits<T>(x0.x, r0); split_bits<T>(x0.y, i0);
-                    split_bits<T>(x1.x, r1); split_bits<T>(x1.y, i1);
+                    uint32_t pr[3], pi[3];
+                    split_pack<T>(x0.x, x1.x, pr);
+                    split_pack<T>(x0.y, x1.y, pi);
 #pragma unroll
                     for (int q = 0; q < T; ++q) {
-                        w[q][e / 2] = pack_hi(r0[q], r1[q]);
-                        w[T + q][e / 2] = pack_hi(i0[q], i1[q]);
+                        w[q][e / 2] = pr[q];
+                        w[T + q][e / 2] = pi[q];
                     }
                 }
                 bf16* dst = it.out + (int64_t)(a + it.rt * r) * it.o_ld + ip;
@@ -1183,13 +1202,13 @@ __device__ __forceinline__ void cat_store_g(uint8_t* sA, const float2 (&v)[CAT_I
         uint32_t w[2 * T][4];
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
-            uint32_t r0[3], i0[3], r1[3], i1[3];
-            split_bits<T>(v[u][e].x, r0); split_bits<T>(v[u][e].y, i0);
-            split_bits<T>(v[u][e + 1].x, r1); split_bits<T>(v[u][e + 1].y, i1);
+            uint32_t pr[3], pi[3];
+            split_pack<T>(v[u][e].x, v[u][e + 1].x, pr);
+            split_pack<T>(v[u][e].y, v[u][e + 1].y, pi);
 #pragma unroll
             for (int q = 0; q < T; ++q) {
-                w[q][e / 2] = pack_hi(r0[q], r1[q]);
-                w[T + q][e / 2] = pack_hi(i0[q], i1[q]);
+                w[q][e / 2] = pr[q];
+                w[T + q][e / 2] = pi[q];
             }
         }
         const int off = canon_off(i, kc, sbo);
@@ -1229,13 +1248,13 @@ __device__ __forceinline__ void cat_build_b(uint8_t* sBp, uint8_t* sBn, const Ca
             const int k = kc * 8 + e;
             if (n < it.rank && k < K) u0 = __ldg(it.fac + k + (int64_t)K * n);
             if (n < it.rank && k + 1 < K) u1 = __ldg(it.fac + k + 1 + (int64_t)K * n);
-            uint32_t r0[3], i0[3], r1[3], i1[3];
-            split_bits<T>(u0.x, r0); split_bits<T>(u0.y, i0);
-            split_bits<T>(u1.x, r1); split_bits<T>(u1.y, i1);
+            uint32_t pr[3], pi[3];
+            split_pack<T>(u0.x, u1.x, pr);
+            split_pack<T>(u0.y, u1.y, pi);
 #pragma unroll
             for (int q = 0; q < T; ++q) {
-                wr[q][e / 2] = pack_hi(r0[q], r1[q]);
-                wi[q][e / 2] = pack_hi(i0[q], i1[q]);
+                wr[q][e / 2] = pr[q];
+                wi[q][e / 2] = pi[q];
             }
         }
 #pragma unroll
