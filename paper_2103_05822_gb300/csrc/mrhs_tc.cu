@@ -133,34 +133,13 @@ __device__ __forceinline__ void cp16(void* dst, const void* src, int bytes) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(bytes));
 }
 
-// v = t0 + t1 (+ t2) in bfloat16 terms, each term as the high half of a 32-bit
-// word (the bfloat16 bit pattern): round the magnitude to 8 significant bits by
-// adding half a unit of the 16 dropped bits, subtract exactly, repeat.  Three
-// terms hold every FP32 value exactly (8 + 8 + 8 significant bits).
-template <int T>
-__device__ __forceinline__ void split_bits(float v, uint32_t* t) {
-    const uint32_t h = (__float_as_uint(v) + 0x8000u) & 0xffff0000u;
-    t[0] = h;
-    const float r = v - __uint_as_float(h);
-    const uint32_t m = (__float_as_uint(r) + 0x8000u) & 0xffff0000u;
-    t[1] = m;
-    if (T == 3) t[2] = (__float_as_uint(r - __uint_as_float(m)) + 0x8000u) & 0xffff0000u;
-}
-
-template <int T>
-__device__ __forceinline__ void split_terms(float v, bf16* t) {
-    uint32_t b[3];
-    split_bits<T>(v, b);
-#pragma unroll
-    for (int q = 0; q < T; ++q) t[q] = __ushort_as_bfloat16((unsigned short)(b[q] >> 16));
-}
-
-// Two values split at once, one word per term (x0 in the low half, x1 in the high half):
-// the hardware conversion rounds both to bfloat16 (to nearest, ties to even), the
-// remainders are exact in FP32, and the same again; with T = 3 the last remainder has at
-// most 8 significant bits, so the three terms hold each value exactly, as with
-// split_bits.  Rounding to nearest is odd in its argument: the terms of -x are the terms
-// of x, negated.  Half the instructions of two split_bits calls and the packing.
+// v = t0 + t1 (+ t2) in bfloat16 terms, two values at once, one 32-bit word per term
+// (x0's term in the low half, x1's in the high half): the hardware conversion rounds
+// both to bfloat16 (to nearest, ties to even), the remainders are exact in FP32
+// (within one bfloat16 unit of the value), and the same again.  Each remainder has at
+// most 16, then 8 significant bits, so three terms hold every FP32 value exactly (down
+// to where the remainders become FP32 subnormals, below about 1e-30).  Rounding to
+// nearest is odd in its argument: the terms of -x are the terms of x, negated.
 template <int T>
 __device__ __forceinline__ void split_pack(float x0, float x1, uint32_t (&w)[3]) {
     uint32_t h;
@@ -176,20 +155,14 @@ __device__ __forceinline__ void split_pack(float x0, float x1, uint32_t (&w)[3])
     }
 }
 
-// two split values -> one word per term plane (lower index in the low half)
-__device__ __forceinline__ uint32_t pack_hi(uint32_t lo_word, uint32_t hi_word) {
-    return __byte_perm(lo_word, hi_word, 0x7632);
-}
-
 template <int T>
 __device__ __forceinline__ void store_planes(bf16* base, int64_t ps, int64_t idx, float2 v) {
-    bf16 tr[3], ti[3];
-    split_terms<T>(v.x, tr);
-    split_terms<T>(v.y, ti);
+    uint32_t w[3];
+    split_pack<T>(v.x, v.y, w);  // term p of the real part in the low half, of the imaginary part in the high
 #pragma unroll
     for (int p = 0; p < T; ++p) {
-        base[p * ps + idx] = tr[p];
-        base[(T + p) * ps + idx] = ti[p];
+        base[p * ps + idx] = __ushort_as_bfloat16((unsigned short)(w[p] & 0xffffu));
+        base[(T + p) * ps + idx] = __ushort_as_bfloat16((unsigned short)(w[p] >> 16));
     }
 }
 
